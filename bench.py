@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""Throughput of the photon-packet life cycle on GB300.
+
+One step = one skirt_trace call over the whole workload: the exponential-disk
+galaxy on a 256^3 grid, 1e8 packets at one optical wavelength, three
+512x512 instruments (inclinations 0/60/90 deg), traced in the mixed form
+(FP32 traversal and phase-function sampling, FP64 optical-depth sums and
+tallies) by one persistent launch replayed from a CUDA graph.  Inputs are
+resident in HBM when the timed region starts; L2 is flushed (256 MB write)
+before every timed step.
+
+Reported next to it: the plain FP64 form on 1e7 packets of the same
+workload, the end-to-end time through the C ABI with pinned host buffers,
+the roofline of the trace kernel, and the CPU FP64 oracle timed on a sample.
+
+`--impl reference` times the oracle (the slow, plain CPU program the
+parity tests compare against) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "photon packets×wavelengths/s on 1 GB300 (FP32+batched vs plain FP64, at 1e-4 rel)"
+UNIT = "packets*lambda/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--packets", type=float, default=1e8)
+    ap.add_argument("--grid", type=int, default=256)
+    ap.add_argument("--fp64-packets", type=float, default=1e7)
+    ap.add_argument("--cpu-packets", type=int, default=60000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload(args):
+    from paper_1705_04702_gb300 import workloads as W
+    return W.disk_problem(int(args.packets), n=args.grid, nlambda=1, npx=512)
+
+
+def config_of(args, prob, extra=None):
+    c = {
+        "workload": f"exponential-disk galaxy, {args.grid}^3 Cartesian grid, 1 wavelength (0.55 um), "
+                    f"{int(args.packets):.0e} packets, 3 instruments 512x512 (i=0/60/90)",
+        "grid": args.grid,
+        "nlambda": prob.wl.n,
+        "packets_per_step": prob.total_packets,
+        "instruments": len(prob.instruments),
+        "npx": 512,
+        "l2": "flushed by a 256 MB write before every timed step",
+    }
+    if extra:
+        c.update(extra)
+    return c
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    mx.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[4:8]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ reference
+def run_reference(args):
+    """The CPU FP64 oracle on a bounded sample per step (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    prob = workload(args)
+    per_step = max(1, min(8000, int(args.packets)))
+    for _ in range(args.warmup):
+        oracle.trace(prob, 0, per_step)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        lo = (s + 1) * per_step
+        oracle.trace(prob, lo, lo + per_step)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": config_of(args, prob, {"sample_per_step": per_step}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} packets per step of the {int(args.packets):.0e}-packet workload"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------- ours
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    # the CPU baseline runs before any GPU work (rank 0, single GPU only)
+    cpu = None
+    prob = workload(args)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        n = args.cpu_packets
+        t0 = time.perf_counter()
+        oracle.trace(prob, 0, n)
+        dt = time.perf_counter() - t0
+        cpu = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"packets 0..{n - 1} of the {int(args.packets):.0e}-packet workload, "
+                         f"single-threaded FP64, {dt:.1f} s"}
+
+    import torch
+    from paper_1705_04702_gb300 import build
+    build.build()
+    from paper_1705_04702_gb300 import skirt as S
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    seed = 1 + rank  # independent replicas: every rank traces its own packets
+    prob.seed = seed
+    grid = S.Grid(prob.grid)
+    n = prob.wl.n
+    npix = sum(i.npx * i.npx for i in prob.instruments) * n
+    absorbed = torch.zeros((grid.ncell, n), dtype=torch.float64, device="cuda")
+    images = torch.zeros(npix, dtype=torch.float64, device="cuda")
+    sed = torch.zeros((len(prob.instruments), n), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    tables = S.Tables(prob.wl)
+    ins = S.make_instruments(prob.instruments)
+    src = S.make_source(prob.source)
+    opts = S.skirt_trace_opts_default()
+    opts.precision = S.PREC_MIXED
+    opts.schedule = S.SCHED_PERSISTENT
+    opts.use_graph = 1
+    tune = None
+    if args.autotune:
+        S.skirt_autotune(grid.h, src, tables.c, prob.npk, seed, ins, opts, 0.01, absorbed, images, sed,
+                         stream=stream.cuda_stream)
+        tune = {"block": opts.block, "chunk": opts.chunk, "blocks_per_sm": opts.blocks_per_sm}
+
+    def step():
+        return S.skirt_trace(grid.h, src, tables.c, prob.npk, seed, ins, opts, absorbed, images, sed,
+                             stream=stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    kernel_ms = []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    led = None
+    for _ in range(args.steps):
+        flush.zero_()
+        _, led, _ = step()
+        kernel_ms.append(led["kernel_ms"])
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if dist is not None:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    packets = prob.total_packets
+    value = packets * world * args.steps / elapsed
+
+    # ---- roofline of the trace kernel: algorithmic bytes per launch
+    kr_b = 4
+    per_launch_bytes = (kr_b * (led["deposit_steps"] + led["locate_steps"] + led["peel_steps"])
+                        + 16 * led["deposit_steps"]
+                        + 16 * (packets + led["scatterings"]) * len(prob.instruments))
+    k_ms = float(np.mean(kernel_ms))
+    achieved = per_launch_bytes / (k_ms / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "peak_source": peak_kind, "kernel": "trace_kernel<float>",
+            "kernel_ms": k_ms, "algorithmic_bytes_per_launch": per_launch_bytes,
+            "per_packet": {"deposit_steps": led["deposit_steps"] / packets,
+                           "locate_steps": led["locate_steps"] / packets,
+                           "peel_steps": led["peel_steps"] / packets,
+                           "scatterings": led["scatterings"] / packets}}
+
+    # ---- plain FP64 form, one launch per wavelength, on a sample
+    fp64 = None
+    if args.fp64_packets > 0:
+        p64 = prob.with_packets(int(args.fp64_packets))
+        o64 = S.skirt_trace_opts_default()
+        o64.precision = S.PREC_FP64
+        o64.schedule = S.SCHED_PER_LAMBDA
+        S.skirt_trace(grid.h, src, tables.c, p64.npk, seed, ins, o64, absorbed, images, sed,
+                      stream=stream.cuda_stream)
+        barrier()
+        t0 = time.perf_counter()
+        _, l64, _ = S.skirt_trace(grid.h, src, tables.c, p64.npk, seed, ins, o64, absorbed, images, sed,
+                                  stream=stream.cuda_stream)
+        barrier()
+        dt64 = time.perf_counter() - t0
+        fp64 = {"value": p64.total_packets / dt64, "unit": UNIT, "packets": p64.total_packets,
+                "kernel_ms": l64["kernel_ms"], "precision": "fp64", "schedule": "per-wavelength launch"}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_kr = torch.from_numpy(np.ascontiguousarray(prob.grid.kr, dtype=np.float32).ravel()).pin_memory()
+        h_abs = torch.zeros((grid.ncell, n), dtype=torch.float64).pin_memory()
+        h_img = torch.zeros(npix, dtype=torch.float64).pin_memory()
+        h_sed = torch.zeros((len(prob.instruments), n), dtype=torch.float64).pin_memory()
+        ksteps = min(args.steps, 3)
+
+        def e2e_step():
+            g2 = S.Grid(prob.grid, kr=h_kr)
+            S.skirt_trace(g2.h, src, tables.c, prob.npk, seed, ins, opts, h_abs, h_img, h_sed,
+                          stream=stream.cuda_stream)
+            g2.close()
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ksteps):
+            e2e_step()
+        barrier()
+        dte = (time.perf_counter() - t0) / ksteps
+        h2d = h_kr.numel() * 4
+        d2h = (h_abs.numel() + h_img.numel() + h_sed.numel()) * 8
+        e2e = {"value": packets * world / dte, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": ksteps}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": config_of(args, prob, {"precision": "mixed", "schedule": "persistent + CUDA graph",
+                                             "replicas": world, "tuning": tune or {
+                                                 "block": opts.block, "chunk": opts.chunk,
+                                                 "blocks_per_sm": opts.blocks_per_sm}}),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps * (1 + len(prob.instruments)),
+            "clocks": clk,
+            "plain_fp64": fp64,
+            "speedup_vs_plain_fp64": (value / world / fp64["value"]) if fp64 else None,
+        }
+        print(json.dumps(line), flush=True)
+    grid.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+// Internal declarations shared by the translation units of libskirt.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "skirt.h"
+
+namespace skirt {
+
+// ---------------------------------------------------------------------------
+// Counter-based random numbers: Philox4x32 with 10 rounds (Salmon et al.,
+// SC'11).  Round: multiply words 0 and 2 by the two Philox multipliers, swap
+// the halves across and xor the high halves with the other words and the
+// round key; the key advances by the two Weyl increments between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        uint32_t h0 = __umulhi(m0, c.x), l0 = m0 * c.x;
+        uint32_t h1 = __umulhi(m1, c.z), l1 = m1 * c.z;
+        c = make_uint4(h1 ^ c.y ^ k0, l1, h0 ^ c.w ^ k1, l0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Uniform deviate in (0, 1): (top 23 bits + 1/2) * 2^-23.  Exactly
+// representable in FP32, so both precisions see identical values.
+__device__ __forceinline__ float u01f(uint32_t x) { return ((float)(x >> 9) + 0.5f) * 1.1920928955078125e-7f; }
+
+// Per-instrument constants (host-computed in FP64, FP32 copies for the mixed form).
+struct InstrDev {
+    double kobs[3], e1[3], e2[3];
+    double half_fov, inv_dpx, flux_norm;
+    float kobs_f[3], e1_f[3], e2_f[3];
+    float half_fov_f, inv_dpx_f;
+    int npx;
+    long long img_off;  // element offset of this instrument in the images array
+};
+
+enum { ERRBIT_EVENT_CAP = 1, ERRBIT_SOURCE = 2, ERRBIT_NONFINITE = 4 };
+
+struct TraceArgs {
+    const float* kr32;
+    const double* kr64;
+    int nx, ny, nz;
+    double lo[3], d[3], hi[3];
+    int nlambda;
+    const double* kscale;
+    const double* albedo;
+    const double* g;
+    const double* L0;                      // luminosity per packet at each wavelength
+    const unsigned long long* offsets;     // [nlambda + 1] prefix sums of packet counts
+    unsigned long long total;
+    int src_kind;
+    double src_pos[3], src_dir[3], h_R, h_z;
+    const double* cdf;                     // dust source: [nlambda][ncell] cumulative, normalised
+    int ninstr;
+    const InstrDev* ins;
+    double* absorbed;                      // [ncell][nlambda]
+    double* images;                        // per instrument [npx*npx][nlambda]
+    double* oof;                           // [ninstr][nlambda] peel-offs outside the frame
+    double* ledger;                        // [nlambda][4]
+    unsigned long long* counters;          // [4]
+    unsigned int* err;
+    int nrec;
+    double* records;                       // [nlambda][nrec][8]
+    double w_min;
+    int max_events;
+    int peel;
+    uint32_t key0, key1, phase;
+    unsigned long long* queue;
+    int chunk;
+    int persistent;
+    unsigned long long q_base, q_count;    // per-wavelength schedule: this launch's packets
+};
+
+// trace.cu
+cudaError_t launch_trace(const TraceArgs& a, int precision, int block, int grid, cudaStream_t s);
+cudaError_t trace_occupancy(int precision, int block, int* blocks_per_sm);
+size_t trace_smem_bytes(int ninstr, int block);
+// sed[q][lambda] += sign * (sum over the pixels of images_q) + oof[q][lambda] (oof may be NULL)
+cudaError_t launch_sed_finalize(const double* images, const double* oof, double* sed, int ninstr,
+                                const int* npx_host, int nlambda, double sign, cudaStream_t s);
+cudaError_t launch_f32_to_f64(const float* in, double* out, long long n, unsigned int* bad,
+                              cudaStream_t s);
+
+// Device buffer that only grows.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t n)
+    {
+        if (n <= bytes && p) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc(&p, n ? n : 16);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        bytes = n ? n : 16;
+        return cudaSuccess;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
+// Pinned host buffer that only grows.
+struct PinnedBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t n)
+    {
+        if (n <= bytes && p) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMallocHost(&p, n ? n : 16);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        bytes = n ? n : 16;
+        return cudaSuccess;
+    }
+    void release()
+    {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
+// error reporting shared by the translation units (api.cu)
+int set_error(int code, const char* fmt, ...);
+
+}  // namespace skirt
+
+// The grid handle: the dust densities on the device and the scratch memory
+// that the calls on this grid reuse.  Not thread-safe: one call at a time.
+struct skirt_grid_s {
+    int device = 0;
+    int sm_count = 0;
+    int nx = 0, ny = 0, nz = 0;
+    long long ncell = 0;
+    double bbox[6] = {0, 0, 0, 0, 0, 0};
+    float* kr32 = nullptr;
+    double* kr64 = nullptr;
+    skirt::DevBuf scratch;  // per-call tables, accumulators, work queue
+    skirt::DevBuf stage;    // device images of host outputs
+    skirt::DevBuf cdf;      // dust source: [nlambda][ncell] cumulative distributions
+    skirt::DevBuf cdf_aux;  // dust source: tile sums and totals
+    skirt::PinnedBuf pinned;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<unsigned char> gkey;
+};
+
+namespace skirt {
+// dust_source.cu: per-wavelength cumulative distribution of emission[cell][lambda]
+// over the cells, normalised to 1, into grid->cdf.  INVALID_ARG when a
+// wavelength with packets has no (or non-finite / negative) emission.
+int build_dust_cdf(skirt_grid_s* g, const double* emission, int nlambda, const uint64_t* npk, cudaStream_t s);
+}  // namespace skirt

@@ -1,0 +1,262 @@
+"""Thin ctypes binding of libskirt (include/skirt.h).
+
+Argument marshalling only: every step of the photon-packet life cycle runs in
+the library's CUDA kernels.  PyTorch provides device memory and streams.
+Importing this module loads ``lib/libskirt.so`` and raises ImportError if it
+has not been built -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libskirt.so")
+
+# status codes
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_EVENT_CAP, ERR_NONFINITE, ERR_SOURCE, ERR_NO_DEVICE = range(8)
+SRC_POINT, SRC_DISK, SRC_BEAM, SRC_DUST = range(4)
+PREC_FP64, PREC_MIXED = 0, 1
+SCHED_PER_LAMBDA, SCHED_PERSISTENT = 0, 1
+REC_FIELDS = 8
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class skirt_source(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("pos", ctypes.c_double * 3), ("dir", ctypes.c_double * 3),
+                ("h_R", ctypes.c_double), ("h_z", ctypes.c_double), ("emission", ctypes.c_void_p)]
+
+
+class skirt_wavelengths(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("kscale", _dp), ("albedo", _dp), ("g", _dp), ("lsrc", _dp)]
+
+
+class skirt_instrument(ctypes.Structure):
+    _fields_ = [("distance", ctypes.c_double), ("inclination_deg", ctypes.c_double),
+                ("azimuth_deg", ctypes.c_double), ("fov", ctypes.c_double), ("npx", ctypes.c_int)]
+
+
+class skirt_trace_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("schedule", ctypes.c_int), ("w_min", ctypes.c_double),
+                ("max_events", ctypes.c_int), ("peel", ctypes.c_int), ("accumulate", ctypes.c_int),
+                ("block", ctypes.c_int), ("chunk", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("use_graph", ctypes.c_int), ("phase", ctypes.c_uint32), ("nrec", ctypes.c_int),
+                ("records", ctypes.c_void_p)]
+
+
+class skirt_ledger(ctypes.Structure):
+    _fields_ = [("emitted", ctypes.c_double), ("absorbed", ctypes.c_double), ("escaped", ctypes.c_double),
+                ("residual", ctypes.c_double), ("scatterings", ctypes.c_double),
+                ("deposit_steps", ctypes.c_double), ("locate_steps", ctypes.c_double),
+                ("peel_steps", ctypes.c_double), ("status_bits", ctypes.c_int), ("kernel_ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libskirt.so is not built ({LIB_PATH}); run paper_1705_04702_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64
+    L.skirt_last_error.restype = ctypes.c_char_p
+    L.skirt_last_error.argtypes = []
+    L.skirt_version.restype = ctypes.c_char_p
+    L.skirt_version.argtypes = []
+    L.skirt_trace_opts_default.argtypes = [ctypes.POINTER(skirt_trace_opts)]
+    L.skirt_trace_opts_default.restype = i
+    L.skirt_grid_create.argtypes = [ctypes.POINTER(vp), i, i, i, _dp, vp]
+    L.skirt_grid_create.restype = i
+    L.skirt_grid_destroy.argtypes = [vp]
+    L.skirt_grid_destroy.restype = i
+    L.skirt_trace.argtypes = [vp, ctypes.POINTER(skirt_source), ctypes.POINTER(skirt_wavelengths),
+                              ctypes.POINTER(u64), u64, ctypes.POINTER(skirt_instrument), i,
+                              ctypes.POINTER(skirt_trace_opts), vp, vp, vp, ctypes.POINTER(skirt_ledger),
+                              _dp, vp]
+    L.skirt_trace.restype = i
+    L.skirt_autotune.argtypes = [vp, ctypes.POINTER(skirt_source), ctypes.POINTER(skirt_wavelengths),
+                                 ctypes.POINTER(u64), u64, ctypes.POINTER(skirt_instrument), i,
+                                 ctypes.POINTER(skirt_trace_opts), ctypes.c_double, vp, vp, vp, vp]
+    L.skirt_autotune.restype = i
+    return L
+
+
+lib = _load()
+
+
+class SkirtError(RuntimeError):
+    def __init__(self, code, where):
+        msg = lib.skirt_last_error().decode(errors="replace")
+        super().__init__(f"{where} failed with status {code}: {msg}")
+        self.code = code
+
+
+def _check(code, where, allow=()):
+    if code != OK and code not in allow:
+        raise SkirtError(code, where)
+    return code
+
+
+def _ptr(x):
+    """Address of a torch tensor / numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+# --------------------------------------------------------------------- C names
+def skirt_version() -> str:
+    return lib.skirt_version().decode()
+
+
+def skirt_trace_opts_default() -> skirt_trace_opts:
+    o = skirt_trace_opts()
+    _check(lib.skirt_trace_opts_default(ctypes.byref(o)), "skirt_trace_opts_default")
+    return o
+
+
+def skirt_grid_create(nx, ny, nz, bbox, kr):
+    """kr: float32 torch tensor (CUDA or CPU) or numpy array of nx*ny*nz values."""
+    h = ctypes.c_void_p()
+    bb = (ctypes.c_double * 6)(*[float(v) for v in bbox])
+    _check(lib.skirt_grid_create(ctypes.byref(h), int(nx), int(ny), int(nz), bb, _ptr(kr)), "skirt_grid_create")
+    return h
+
+
+def skirt_grid_destroy(h):
+    _check(lib.skirt_grid_destroy(h), "skirt_grid_destroy")
+
+
+def skirt_trace(grid, src: skirt_source, wl: skirt_wavelengths, npackets, seed, instruments, opts,
+                absorbed, images, sed, stream=None, allow=(ERR_EVENT_CAP,)):
+    """Marshals to skirt_trace; returns (status, ledger dict, per-wavelength
+    ledger [n, 4])."""
+    npk = np.ascontiguousarray(npackets, dtype=np.uint64)
+    n = wl.n
+    ins_arr = (skirt_instrument * max(len(instruments), 1))(*instruments)
+    led = skirt_ledger()
+    per = np.zeros((n, 4))
+    st = None if stream is None else ctypes.c_void_p(int(stream))
+    code = lib.skirt_trace(grid, ctypes.byref(src), ctypes.byref(wl),
+                           npk.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), int(seed) & (2 ** 64 - 1),
+                           ins_arr, len(instruments), ctypes.byref(opts), _ptr(absorbed), _ptr(images), _ptr(sed),
+                           ctypes.byref(led), per.ctypes.data_as(_dp), st)
+    _check(code, "skirt_trace", allow)
+    return code, led.as_dict(), per
+
+
+def skirt_autotune(grid, src, wl, npackets, seed, instruments, opts, sample_fraction, absorbed, images, sed,
+                   stream=None):
+    npk = np.ascontiguousarray(npackets, dtype=np.uint64)
+    ins_arr = (skirt_instrument * max(len(instruments), 1))(*instruments)
+    st = None if stream is None else ctypes.c_void_p(int(stream))
+    code = lib.skirt_autotune(grid, ctypes.byref(src), ctypes.byref(wl),
+                              npk.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), int(seed) & (2 ** 64 - 1),
+                              ins_arr, len(instruments), ctypes.byref(opts), float(sample_fraction),
+                              _ptr(absorbed), _ptr(images), _ptr(sed), st)
+    _check(code, "skirt_autotune", (ERR_EVENT_CAP,))
+    return opts
+
+
+# ------------------------------------------------------- problem marshalling
+class Tables:
+    """Keeps the host arrays a skirt_wavelengths points into alive."""
+
+    def __init__(self, wl):
+        self.kscale = np.ascontiguousarray(wl.kscale, dtype=np.float64)
+        self.albedo = np.ascontiguousarray(wl.albedo, dtype=np.float64)
+        self.g = np.ascontiguousarray(wl.g, dtype=np.float64)
+        self.lsrc = np.ascontiguousarray(wl.lsrc, dtype=np.float64)
+        self.c = skirt_wavelengths(wl.n, self.kscale.ctypes.data_as(_dp), self.albedo.ctypes.data_as(_dp),
+                                   self.g.ctypes.data_as(_dp), self.lsrc.ctypes.data_as(_dp))
+
+
+def make_source(s, emission=None) -> skirt_source:
+    return skirt_source(int(s.kind), (ctypes.c_double * 3)(*s.pos), (ctypes.c_double * 3)(*s.dir),
+                        float(s.h_R), float(s.h_z), None if emission is None else emission.data_ptr())
+
+
+def make_instruments(instruments):
+    return [skirt_instrument(float(i.distance), float(i.inclination), float(i.azimuth), float(i.fov), int(i.npx))
+            for i in instruments]
+
+
+class Grid:
+    """Owns a skirt grid handle built from a workloads.Grid (or any object with
+    nx, ny, nz, bbox, kr)."""
+
+    def __init__(self, grid, kr=None):
+        import torch
+        self.nx, self.ny, self.nz = grid.nx, grid.ny, grid.nz
+        self.bbox = tuple(grid.bbox)
+        self.ncell = grid.nx * grid.ny * grid.nz
+        if kr is None:
+            kr = torch.from_numpy(np.ascontiguousarray(grid.kr, dtype=np.float32).ravel())
+        self.h = skirt_grid_create(self.nx, self.ny, self.nz, self.bbox, kr)
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            skirt_grid_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def run_problem(prob, grid: Grid | None = None, precision=PREC_MIXED, schedule=SCHED_PERSISTENT, nrec=0,
+                use_graph=False, peel=True, block=0, chunk=0, blocks_per_sm=0, outputs=None, emission=None,
+                device="cuda", stream=None, accumulate=False):
+    """Traces a workloads.Problem on the GPU; returns a dict of torch tensors
+    (absorbed [ncell, n], images list [npx, npx, n], sed [ninstr, n], records)
+    plus ledger information."""
+    import torch
+    own = grid is None
+    if own:
+        grid = Grid(prob.grid)
+    n = prob.wl.n
+    tables = Tables(prob.wl)
+    ins = make_instruments(prob.instruments)
+    img_elems = sum(i.npx * i.npx for i in prob.instruments) * n
+    if outputs is None:
+        absorbed = torch.zeros((grid.ncell, n), dtype=torch.float64, device=device)
+        images = torch.zeros(max(img_elems, 1), dtype=torch.float64, device=device)
+        sed = torch.zeros((max(len(ins), 1), n), dtype=torch.float64, device=device)
+    else:
+        absorbed, images, sed = outputs
+    records = torch.zeros((n, max(nrec, 1), REC_FIELDS), dtype=torch.float64, device=device) if nrec else None
+    o = skirt_trace_opts_default()
+    o.precision = precision
+    o.schedule = schedule
+    o.w_min = prob.w_min
+    o.max_events = prob.max_events
+    o.peel = 1 if peel else 0
+    o.accumulate = 1 if accumulate else 0
+    o.block = block
+    o.chunk = chunk
+    o.blocks_per_sm = blocks_per_sm
+    o.use_graph = 1 if use_graph else 0
+    o.phase = prob.phase
+    o.nrec = nrec
+    o.records = records.data_ptr() if records is not None else None
+    src = make_source(prob.source, emission)
+    code, led, per = skirt_trace(grid.h, src, tables.c, prob.npk, prob.seed, ins, o, absorbed, images, sed,
+                                 stream=stream)
+    imgs, off = [], 0
+    for i in prob.instruments:
+        k = i.npx * i.npx * n
+        imgs.append(images[off:off + k].view(i.npx, i.npx, n))
+        off += k
+    out = {"absorbed": absorbed, "images": imgs, "images_flat": images[:off], "sed": sed[:len(ins)],
+           "records": records[:, :nrec] if records is not None else None, "ledger": led,
+           "ledger_per_lambda": per, "status": code}
+    if own:
+        grid.close()
+    return out

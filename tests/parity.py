@@ -1,0 +1,78 @@
+"""Comparison helpers for GPU-vs-oracle parity (shared by the GPU tests).
+
+Tolerances (derivations in the design notes):
+* FP64 form: the GPU replays the oracle's packet histories with the same
+  Philox streams; the only differences are rounding order (atomic
+  accumulation order, exp/log implementations, reciprocal instead of
+  division).  Per-packet records and tallies agree to 1e-9 relative.
+* Mixed form: FP32 positions, directions and per-cell optical depths.
+  Per-packet continuous quantities within 1e-5 relative; at least 99.9% of
+  packets take the same number of scatterings (a packet whose luminosity
+  lands within FP32 rounding of the w_min threshold may fork); tallies within
+  1e-4 relative for cells / pixels holding at least 1e-6 of the total and an
+  L1-normalised difference below 1e-4.  Pixel indices are decided by FP32
+  positions, so a peel-off within ~|x| 2^-22 of a pixel border can land in
+  the neighbouring pixel: images are compared through their L1-normalised
+  difference with the bound img_l1_bound().
+"""
+import numpy as np
+
+REL_FP64 = 1e-9
+REL_MIXED_PACKET = 1e-5
+REL_MIXED_TALLY = 1e-4
+
+
+def rel_err(a, b, floor):
+    return np.abs(a - b) / np.maximum(np.abs(b), floor)
+
+
+def compare_records(gpu, ref, rel, extent, min_match=1.0):
+    """gpu, ref: [nlambda, nrec, 8].  Returns the fraction of packets whose
+    record matches: same scattering count, escaped/absorbed/residual/peel
+    within rel (floor: 1e-12 of the largest value), last position within
+    rel * extent (absolute)."""
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    assert gpu.shape == ref.shape
+    g = gpu.reshape(-1, 8)
+    r = ref.reshape(-1, 8)
+    same_n = g[:, 0] == r[:, 0]
+    floor = 1e-12 * max(np.abs(r[:, 1:5]).max(), 1e-300)
+    ok_vals = np.all(rel_err(g[:, 1:5], r[:, 1:5], floor) <= rel, axis=1)
+    ok_pos = np.all(np.abs(g[:, 5:8] - r[:, 5:8]) <= rel * extent, axis=1)
+    ok = same_n & ok_vals & ok_pos
+    frac = ok.mean() if ok.size else 1.0
+    assert frac >= min_match, (frac, np.nonzero(~ok)[0][:10], g[~ok][:3], r[~ok][:3])
+    return frac
+
+
+def compare_tally(gpu, ref, rel, significant=1e-6, l1=None):
+    """Element-wise relative check for entries holding >= significant of the
+    total, and an L1-normalised bound over all entries."""
+    gpu = np.asarray(gpu, dtype=np.float64).ravel()
+    ref = np.asarray(ref, dtype=np.float64).ravel()
+    tot = np.abs(ref).sum()
+    if tot == 0:
+        assert np.abs(gpu).sum() == 0
+        return 0.0
+    big = np.abs(ref) >= significant * tot
+    e = rel_err(gpu[big], ref[big], 1e-300)
+    assert e.size == 0 or e.max() <= rel, (e.max(), np.argmax(e))
+    l1n = np.abs(gpu - ref).sum() / tot
+    assert l1n <= (rel if l1 is None else l1), l1n
+    return l1n
+
+
+def img_l1_bound(prob):
+    """Expected L1-normalised image difference from pixel-border
+    reassignment in the mixed form, times a safety factor of 4: each axis
+    moves a fraction ~ 2 * delta / pixel of the peel-offs, delta = |x|max
+    2^-21 (a few FP32 roundings of the position), counted twice in L1."""
+    x0, x1, y0, y1, z0, z1 = prob.grid.bbox
+    xmax = max(abs(v) for v in (x0, x1, y0, y1, z0, z1))
+    delta = xmax * 2.0 ** -21
+    worst = 0.0
+    for ins in prob.instruments:
+        dpx = ins.fov / ins.npx
+        worst = max(worst, 2 * 2 * (2 * delta / dpx))
+    return max(4 * worst, REL_MIXED_TALLY)

@@ -1,0 +1,74 @@
+"""The C ABI library builds, loads and exports every function declared in
+include/skirt.h; host-side validation answers without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def skirt():
+    from paper_1705_04702_gb300 import build
+    build.build()
+    from paper_1705_04702_gb300 import skirt as S
+    return S
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?!typedef)[A-Za-z_][\w\s\*]*?\b(skirt_\w+)\s*\(", text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("skirt_grid_create", "skirt_grid_destroy", "skirt_trace", "skirt_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(skirt):
+    lib = ctypes.CDLL(skirt.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version_and_defaults(skirt):
+    assert "sm_103a" in skirt.skirt_version()
+    o = skirt.skirt_trace_opts_default()
+    assert o.precision == skirt.PREC_MIXED and o.schedule == skirt.SCHED_PERSISTENT
+    assert o.w_min == 1e-4 and o.max_events == 10000 and o.peel == 1
+
+
+def test_null_arguments_are_rejected(skirt):
+    lib = skirt.lib
+    assert lib.skirt_grid_create(None, 4, 4, 4, None, None) == skirt.ERR_INVALID_ARG
+    h = ctypes.c_void_p()
+    bb = (ctypes.c_double * 6)(-1, 1, -1, 1, -1, 1)
+    assert lib.skirt_grid_create(ctypes.byref(h), 0, 4, 4, bb, None) == skirt.ERR_INVALID_ARG
+    bad = (ctypes.c_double * 6)(1, -1, -1, 1, -1, 1)
+    dummy = (ctypes.c_float * 64)()
+    assert lib.skirt_grid_create(ctypes.byref(h), 4, 4, 4, bad, dummy) == skirt.ERR_INVALID_ARG
+    assert b"empty" in lib.skirt_last_error()
+    o = skirt.skirt_trace_opts()
+    assert lib.skirt_trace(None, None, None, None, 0, None, 0, ctypes.byref(o), None, None, None, None, None,
+                           None) == skirt.ERR_INVALID_ARG
+    assert lib.skirt_grid_destroy(None) == skirt.OK
+
+
+def test_no_device_is_reported_not_crashed(skirt):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    bb = (ctypes.c_double * 6)(-1, 1, -1, 1, -1, 1)
+    dummy = (ctypes.c_float * 8)()
+    assert skirt.lib.skirt_grid_create(ctypes.byref(h), 2, 2, 2, bb, dummy) == skirt.ERR_NO_DEVICE

@@ -1,0 +1,188 @@
+"""GPU parity: the CUDA life cycle, called through the C ABI, against the
+FP64 oracle on the same seeded inputs and Philox streams."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1705_04702_gb300 import workloads as W
+
+from parity import (REL_FP64, REL_MIXED_PACKET, REL_MIXED_TALLY, compare_records, compare_tally,
+                    img_l1_bound)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1705_04702_gb300 import build
+    build.build()
+    from paper_1705_04702_gb300 import skirt
+    return skirt
+
+
+def _np(t):
+    return t.detach().cpu().numpy() if t is not None else None
+
+
+def _extent(prob):
+    b = prob.grid.bbox
+    return max(b[1] - b[0], b[3] - b[2], b[5] - b[4])
+
+
+def _check(S, oracle_lib, prob, precision, nrec=0, **kw):
+    nrec = nrec or int(min(prob.npk.max(), 4000))
+    g = S.run_problem(prob, precision=precision, nrec=nrec, **kw)
+    r = oracle_lib.trace(prob, nrec=nrec)
+    fp64 = precision == S.PREC_FP64
+    rel_p = REL_FP64 if fp64 else REL_MIXED_PACKET
+    rel_t = REL_FP64 if fp64 else REL_MIXED_TALLY
+    compare_records(_np(g["records"]), r["records"], rel_p, _extent(prob), 1.0 if fp64 else 0.999)
+    compare_tally(_np(g["absorbed"]), r["absorbed"], rel_t)
+    if prob.instruments:
+        compare_tally(_np(g["sed"]), r["sed"], rel_t, significant=0.0)
+        compare_tally(_np(g["images_flat"]), r["images_flat"], rel_t if fp64 else 1.0,
+                      significant=1e-6 if fp64 else 1.1, l1=rel_t if fp64 else img_l1_bound(prob))
+    led = g["ledger_per_lambda"]
+    np.testing.assert_allclose(led, r["ledger"], rtol=rel_t, atol=1e-300)
+    tot = g["ledger"]
+    closure = abs(tot["emitted"] - tot["absorbed"] - tot["escaped"] - tot["residual"]) / max(tot["emitted"], 1e-300)
+    assert closure < (1e-12 if fp64 else 1e-6), closure
+    if fp64:
+        assert tot["scatterings"] == r["counters"][0]
+    return g, r
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_sphere_c1(S, oracle_lib, precision):
+    prob = W.sphere_problem(100_000)
+    _check(S, oracle_lib, prob, precision)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_disk_multi_wavelength(S, oracle_lib, precision):
+    prob = W.disk_problem(3000, n=64, nlambda=3, npx=64)
+    _check(S, oracle_lib, prob, precision)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_torus_uneven_counts(S, oracle_lib, precision):
+    prob = W.torus_problem(n=48, nlambda=12, packet_scale=2e-4, npx=48)
+    prob.npk[3] = 0  # an empty wavelength in the middle
+    _check(S, oracle_lib, prob, precision)
+
+
+@pytest.mark.parametrize("schedule", [0, 1], ids=["per_lambda", "persistent"])
+def test_schedules_and_launch_shapes_give_identical_histories(S, schedule):
+    """Per-packet histories depend only on (seed, packet, wavelength): every
+    schedule, block size and refill chunk gives bit-identical records."""
+    prob = W.torus_problem(n=32, nlambda=5, packet_scale=1e-4, npx=32)
+    base = S.run_problem(prob, precision=S.PREC_MIXED, schedule=S.SCHED_PERSISTENT, nrec=500)
+    for block, chunk in ((64, 1), (256, 3), (512, 16)):
+        other = S.run_problem(prob, precision=S.PREC_MIXED, schedule=schedule, nrec=500, block=block, chunk=chunk)
+        assert np.array_equal(_np(base["records"]), _np(other["records"]))
+        compare_tally(_np(other["absorbed"]), _np(base["absorbed"]), 1e-12)
+
+
+def test_slab_beam_exact(S):
+    layer = np.array([0.2, 0.3, 0.5, 4.0], dtype=np.float32).astype(np.float64)
+    grid = W.slab_grid(layer)
+    for prec in (S.PREC_FP64, S.PREC_MIXED):
+        prob = W.beam_problem(grid, (0.1, 0.2, 0.0), (0.6, 0.0, 0.8), npackets=1, albedo=0.0)
+        g = S.run_problem(prob, precision=prec, nrec=1)
+        rec = _np(g["records"])[0, 0]
+        tol = 1e-14 if prec == S.PREC_FP64 else 1e-6
+        assert rec[1] == pytest.approx(math.exp(-layer.sum() / 0.8), rel=tol)
+        cum = np.concatenate([[0.0], np.cumsum(layer)]) / 0.8
+        got = _np(g["absorbed"])[:, 0].reshape(grid.nz, -1).sum(axis=1)
+        np.testing.assert_allclose(got, np.exp(-cum[:-1]) - np.exp(-cum[1:]), rtol=tol)
+
+
+def test_edge_cases(S, oracle_lib):
+    # no packets at all
+    prob = W.sphere_problem(0)
+    g = S.run_problem(prob)
+    assert float(g["absorbed"].abs().sum()) == 0 and g["ledger"]["emitted"] == 0
+    # a single packet, a 1x1x1 grid
+    grid = W.uniform_grid(1, kr=0.7)
+    prob = W.Problem("one", grid, W.Source(W.SRC_POINT, (0.1, -0.3, 0.2)), W.single_wavelength(),
+                     np.array([1], np.uint64), [W.Instrument(10.0, 20.0, 10.0, 2.0, 3)])
+    for prec in (0, 1):
+        g = S.run_problem(prob, precision=prec, nrec=1)
+        r = oracle_lib.trace(prob, nrec=1)
+        compare_records(_np(g["records"]), r["records"], REL_FP64 if prec == 0 else REL_MIXED_PACKET, 2.0)
+    # dust-free grid: everything escapes, nothing absorbed
+    prob = W.Problem("empty", W.uniform_grid(8, kr=0.0), W.Source(W.SRC_POINT, (0.0, 0.0, 0.0)),
+                     W.single_wavelength(), np.array([1000], np.uint64), [W.Instrument(10.0, 0.0, 0.0, 2.0, 8)])
+    g = S.run_problem(prob, nrec=10)
+    assert float(g["absorbed"].abs().sum()) == 0
+    assert g["ledger"]["escaped"] == pytest.approx(1.0, rel=1e-12)
+    assert float(g["sed"][0, 0]) == pytest.approx(1.0 / (4 * math.pi * 100), rel=1e-6)
+    # no instruments, and peel-off disabled
+    prob = W.sphere_problem(2000)
+    ref = oracle_lib.trace(prob, peel=False)
+    for p in (True, False):
+        q = W.sphere_problem(2000)
+        if p:
+            q.instruments = []
+        g = S.run_problem(q, precision=0, peel=not p)
+        compare_tally(_np(g["absorbed"]), ref["absorbed"], REL_FP64)
+
+
+def test_event_cap_is_reported(S):
+    prob = W.sphere_problem(100)
+    prob.max_events = 1
+    g = S.run_problem(prob, nrec=100)
+    assert g["status"] == S.ERR_EVENT_CAP
+    assert np.all(_np(g["records"])[0, :, 0] == 1)
+
+
+def test_graph_replay_host_buffers_and_accumulate(S):
+    import torch
+    prob = W.disk_problem(4000, n=32, nlambda=2, npx=32)
+    grid = S.Grid(prob.grid)
+    a = S.run_problem(prob, grid=grid, precision=1)
+    b1 = S.run_problem(prob, grid=grid, precision=1, use_graph=True)
+    b2 = S.run_problem(prob, grid=grid, precision=1, use_graph=True)
+    for b in (b1, b2):
+        compare_tally(_np(b["absorbed"]), _np(a["absorbed"]), 1e-12)
+        compare_tally(_np(b["sed"]), _np(a["sed"]), 1e-12, significant=0.0)
+    # host (pinned and pageable) output buffers give the same tallies
+    n = prob.wl.n
+    npix = sum(i.npx * i.npx for i in prob.instruments) * n
+    for pin in (True, False):
+        outs = (torch.zeros((grid.ncell, n), dtype=torch.float64, pin_memory=pin),
+                torch.zeros(npix, dtype=torch.float64, pin_memory=pin),
+                torch.zeros((len(prob.instruments), n), dtype=torch.float64, pin_memory=pin))
+        h = S.run_problem(prob, grid=grid, precision=1, outputs=outs)
+        compare_tally(h["absorbed"].numpy(), _np(a["absorbed"]), 1e-12)
+        compare_tally(h["sed"].numpy(), _np(a["sed"]), 1e-12, significant=0.0)
+    # accumulate: a second call with another seed adds to the first
+    p2 = W.disk_problem(4000, n=32, nlambda=2, npx=32, seed=7)
+    c = S.run_problem(p2, grid=grid, precision=1)
+    outs = (a["absorbed"].clone(), torch.cat([a["images_flat"].clone()]), a["sed"].clone())
+    acc = S.run_problem(p2, grid=grid, precision=1, outputs=outs, accumulate=True)
+    compare_tally(_np(acc["absorbed"]), _np(a["absorbed"] + c["absorbed"]), 1e-12)
+    compare_tally(_np(acc["sed"]), _np(a["sed"] + c["sed"]), 1e-12, significant=0.0)
+    grid.close()
+
+
+def test_invalid_arguments(S):
+    prob = W.sphere_problem(10)
+    bad = W.sphere_problem(10)
+    bad.wl.albedo[0] = 1.5
+    with pytest.raises(S.SkirtError) as e:
+        S.run_problem(bad)
+    assert e.value.code == S.ERR_INVALID_ARG
+    bad = W.sphere_problem(10)
+    bad.source = W.Source(W.SRC_POINT, (5.0, 0.0, 0.0))
+    with pytest.raises(S.SkirtError):
+        S.run_problem(bad)
+    g = prob.grid
+    g2 = W.Grid(g.nx, g.ny, g.nz, g.bbox, g.kr.copy())
+    g2.kr[0, 0, 0] = np.nan
+    with pytest.raises(S.SkirtError):
+        S.Grid(g2)
