@@ -199,6 +199,14 @@ int skirt_autotune(skirt_grid_t grid, const skirt_source* src, const skirt_wavel
                    skirt_trace_opts* opts, double sample_fraction, double* absorbed,
                    double* images, double* sed, void* stream);
 
+/* Microbenchmarks for the rooflines of the trace kernel (no counterpart in
+ * the paper, which ran on CPUs): kind 0 FP64 FMA rate, 1 FP32 FMA rate,
+ * 2 FP32<->FP64 conversion rate, 3 random-address red.global.add.f64 into a
+ * table of `size` doubles, 4 random FP32 gathers from a table of `size`
+ * floats.  *rate receives operations per second, *ms the kernel time.
+ * Allocates and frees its own device buffers.  Errors: INVALID_ARG, CUDA. */
+int skirt_microbench(int kind, long long size, double* rate, float* ms);
+
 #ifdef __cplusplus
 }
 #endif

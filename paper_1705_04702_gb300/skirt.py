@@ -81,6 +81,8 @@ def _load():
                                  ctypes.POINTER(u64), u64, ctypes.POINTER(skirt_instrument), i,
                                  ctypes.POINTER(skirt_trace_opts), ctypes.c_double, vp, vp, vp, vp]
     L.skirt_autotune.restype = i
+    L.skirt_microbench.argtypes = [i, ctypes.c_longlong, _dp, ctypes.POINTER(ctypes.c_float)]
+    L.skirt_microbench.restype = i
     return L
 
 
@@ -161,6 +163,14 @@ def skirt_autotune(grid, src, wl, npackets, seed, instruments, opts, sample_frac
                               _ptr(absorbed), _ptr(images), _ptr(sed), st)
     _check(code, "skirt_autotune", (ERR_EVENT_CAP,))
     return opts
+
+
+def skirt_microbench(kind, size=0):
+    """Returns (operations per second, kernel ms) of microbenchmark `kind`."""
+    rate = ctypes.c_double()
+    ms = ctypes.c_float()
+    _check(lib.skirt_microbench(int(kind), int(size), ctypes.byref(rate), ctypes.byref(ms)), "skirt_microbench")
+    return rate.value, ms.value
 
 
 # ------------------------------------------------------- problem marshalling

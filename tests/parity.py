@@ -26,23 +26,40 @@ def rel_err(a, b, floor):
     return np.abs(a - b) / np.maximum(np.abs(b), floor)
 
 
-def compare_records(gpu, ref, rel, extent, min_match=1.0):
-    """gpu, ref: [nlambda, nrec, 8].  Returns the fraction of packets whose
-    record matches: same scattering count, escaped/absorbed/residual/peel
-    within rel (floor: 1e-12 of the largest value), last position within
-    rel * extent (absolute)."""
+def record_scales(prob):
+    """Per-wavelength scales of the record fields: the packet's launch
+    luminosity L0 for escaped/absorbed/residual, L0 times the summed
+    peel-off normalisation 1/(4 pi d^2) for the peeled flux, the grid extent
+    for the position."""
+    import math
+    L0 = np.where(prob.npk > 0, prob.wl.lsrc / np.maximum(prob.npk, 1).astype(np.float64), 0.0)
+    norm = sum(1.0 / (4 * math.pi * i.distance ** 2) for i in prob.instruments)
+    b = prob.grid.bbox
+    extent = max(b[1] - b[0], b[3] - b[2], b[5] - b[4])
+    return L0, norm, extent
+
+
+def compare_records(gpu, ref, prob, rel, min_match=1.0):
+    """gpu, ref: [nlambda, nrec, 8] records of the same packets.  A packet
+    matches when it took the same number of scatterings and every other field
+    agrees within rel of its scale (record_scales).  Returns the matching
+    fraction over packets that exist; asserts it is >= min_match."""
     gpu = np.asarray(gpu, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
     assert gpu.shape == ref.shape
-    g = gpu.reshape(-1, 8)
-    r = ref.reshape(-1, 8)
-    same_n = g[:, 0] == r[:, 0]
-    floor = 1e-12 * max(np.abs(r[:, 1:5]).max(), 1e-300)
-    ok_vals = np.all(rel_err(g[:, 1:5], r[:, 1:5], floor) <= rel, axis=1)
-    ok_pos = np.all(np.abs(g[:, 5:8] - r[:, 5:8]) <= rel * extent, axis=1)
-    ok = same_n & ok_vals & ok_pos
+    L0, norm, extent = record_scales(prob)
+    nrec = gpu.shape[1]
+    exists = np.arange(nrec)[None, :] < prob.npk[:, None]
+    scale = np.empty(gpu.shape[:2] + (7,))
+    scale[..., 0:3] = L0[:, None, None]
+    scale[..., 3] = (L0 * max(norm, 1e-300))[:, None]
+    scale[..., 4:7] = extent
+    err = np.abs(gpu[..., 1:] - ref[..., 1:]) / np.maximum(scale, 1e-300)
+    ok = (gpu[..., 0] == ref[..., 0]) & np.all(err <= rel, axis=-1)
+    ok = ok[exists]
     frac = ok.mean() if ok.size else 1.0
-    assert frac >= min_match, (frac, np.nonzero(~ok)[0][:10], g[~ok][:3], r[~ok][:3])
+    bad = np.argwhere(exists & ~((gpu[..., 0] == ref[..., 0]) & np.all(err <= rel, axis=-1)))
+    assert frac >= min_match, (frac, bad[:10], gpu[tuple(bad[:3].T)], ref[tuple(bad[:3].T)])
     return frac
 
 

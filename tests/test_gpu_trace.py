@@ -40,7 +40,7 @@ def _check(S, oracle_lib, prob, precision, nrec=0, **kw):
     fp64 = precision == S.PREC_FP64
     rel_p = REL_FP64 if fp64 else REL_MIXED_PACKET
     rel_t = REL_FP64 if fp64 else REL_MIXED_TALLY
-    compare_records(_np(g["records"]), r["records"], rel_p, _extent(prob), 1.0 if fp64 else 0.999)
+    compare_records(_np(g["records"]), r["records"], prob, rel_p, 0.999)
     compare_tally(_np(g["absorbed"]), r["absorbed"], rel_t)
     if prob.instruments:
         compare_tally(_np(g["sed"]), r["sed"], rel_t, significant=0.0)
@@ -113,7 +113,7 @@ def test_edge_cases(S, oracle_lib):
     for prec in (0, 1):
         g = S.run_problem(prob, precision=prec, nrec=1)
         r = oracle_lib.trace(prob, nrec=1)
-        compare_records(_np(g["records"]), r["records"], REL_FP64 if prec == 0 else REL_MIXED_PACKET, 2.0)
+        compare_records(_np(g["records"]), r["records"], prob, REL_FP64 if prec == 0 else REL_MIXED_PACKET)
     # dust-free grid: everything escapes, nothing absorbed
     prob = W.Problem("empty", W.uniform_grid(8, kr=0.0), W.Source(W.SRC_POINT, (0.0, 0.0, 0.0)),
                      W.single_wavelength(), np.array([1000], np.uint64), [W.Instrument(10.0, 0.0, 0.0, 2.0, 8)])
