@@ -147,6 +147,9 @@ typedef struct {
     int blocks_per_sm; /* persistent grid = blocks_per_sm x SM count; 0 = from occupancy */
     int use_graph;     /* 1: record the launch sequence in a CUDA graph, cached on the grid
                           and replayed by later calls with identical arguments */
+    int step_min;      /* mixed form: a warp keeps stepping cells while at least step_min of
+                          its lanes are inside a traversal, then handles the events of the
+                          idle lanes together (1..32; 0 = default 16) */
     uint32_t phase;    /* random-stream phase: 0 stellar, 1 dust re-emission (< 256) */
     int nrec;          /* >= 0: per-packet records for packet indices < nrec */
     double* records;   /* device-or-host double[n][nrec][8]: scatterings, escaped, absorbed,

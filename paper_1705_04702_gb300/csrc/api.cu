@@ -284,8 +284,10 @@ int validate(skirt_grid_t g, const skirt_source* src, const skirt_wavelengths* w
         return fail(SKIRT_ERR_INVALID_ARG, "unknown precision %d", opts->precision);
     if (opts->schedule != SKIRT_SCHED_PER_LAMBDA && opts->schedule != SKIRT_SCHED_PERSISTENT)
         return fail(SKIRT_ERR_INVALID_ARG, "unknown schedule %d", opts->schedule);
-    if (opts->block != 0 && (opts->block < 32 || opts->block > 1024 || opts->block % 32))
-        return fail(SKIRT_ERR_INVALID_ARG, "block must be a multiple of 32 in [32, 1024]");
+    if (opts->block != 0 && (opts->block < 32 || opts->block % 32 ||
+                             opts->block > (opts->precision == SKIRT_PREC_MIXED ? 256 : 512)))
+        return fail(SKIRT_ERR_INVALID_ARG, "block must be a multiple of 32 up to 256 (mixed) or 512 (FP64)");
+    if (opts->step_min < 0 || opts->step_min > 32) return fail(SKIRT_ERR_INVALID_ARG, "step_min must be in [0, 32]");
     if (opts->chunk < 0 || opts->chunk > (1 << 20)) return fail(SKIRT_ERR_INVALID_ARG, "chunk out of range");
     if (opts->blocks_per_sm < 0 || opts->blocks_per_sm > 64) return fail(SKIRT_ERR_INVALID_ARG, "blocks_per_sm out of range");
     if (opts->phase > 255) return fail(SKIRT_ERR_INVALID_ARG, "phase must be < 256");
@@ -421,6 +423,7 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
     A.phase = opts->phase;
     A.queue = (unsigned long long*)(dp + L.queue);
     A.chunk = opts->chunk > 0 ? opts->chunk : 4;
+    A.step_min = opts->step_min > 0 ? opts->step_min : 16;
 
     const int block = opts->block > 0 ? opts->block : 256;
     int bps = opts->blocks_per_sm;
@@ -429,8 +432,8 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
         if (bps < 1) bps = 1;
     }
     const int pgrid = g->sm_count * bps;
-    const size_t smem = trace_smem_bytes(A.ninstr, block);
-    if (smem > 48 * 1024) return fail(SKIRT_ERR_INVALID_ARG, "block too large for the shared-memory budget");
+    if (opts->precision == SKIRT_PREC_FP64 && trace_smem_bytes(A.ninstr, block) > 48 * 1024)
+        return fail(SKIRT_ERR_INVALID_ARG, "block too large for the shared-memory budget");
 
     // ---- the device work of one call (recorded into a graph when asked)
     auto enqueue = [&](cudaStream_t s, bool events) -> int {
@@ -572,11 +575,12 @@ extern "C" int skirt_autotune(skirt_grid_t g, const skirt_source* src, const ski
     o.accumulate = 0;
     o.nrec = 0;
     o.records = nullptr;
-    const int blocks[4] = {64, 128, 256, 512};
+    const int blocks[4] = {64, 128, 256, o.precision == SKIRT_PREC_MIXED ? 256 : 512};
     const int chunks[5] = {1, 2, 4, 8, 16};
     float best = 1e30f;
     int bb = 256, bc = 4, bbps = 0;
     for (int bi = 0; bi < 4; ++bi) {
+        if (bi > 0 && blocks[bi] == blocks[bi - 1]) continue;
         int maxbps = 0;
         CK(trace_occupancy(o.precision, blocks[bi], &maxbps));
         if (maxbps < 1) continue;

@@ -79,12 +79,18 @@ struct TraceArgs {
     int chunk;
     int persistent;
     unsigned long long q_base, q_count;    // per-wavelength schedule: this launch's packets
+    int step_min;                          // mixed form: lanes still stepping below which a warp
+                                           // switches to handling the events of its idle lanes
 };
 
-// trace.cu
+// trace.cu (FP64 form; dispatches the mixed form to trace_mixed.cu)
 cudaError_t launch_trace(const TraceArgs& a, int precision, int block, int grid, cudaStream_t s);
 cudaError_t trace_occupancy(int precision, int block, int* blocks_per_sm);
 size_t trace_smem_bytes(int ninstr, int block);
+// trace_mixed.cu
+cudaError_t launch_trace_mixed(const TraceArgs& a, int block, int grid, cudaStream_t s);
+cudaError_t trace_mixed_occupancy(int block, int* blocks_per_sm);
+size_t trace_mixed_smem_bytes(int ninstr, int block);
 // sed[q][lambda] += sign * (sum over the pixels of images_q) + oof[q][lambda] (oof may be NULL)
 cudaError_t launch_sed_finalize(const double* images, const double* oof, double* sed, int ninstr,
                                 const int* npx_host, int nlambda, double sign, cudaStream_t s);

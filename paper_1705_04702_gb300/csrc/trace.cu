@@ -1,9 +1,11 @@
-// Photon-packet life cycle on the GPU: one packet per thread, written as a
-// per-thread state machine so that every iteration of the main loop does one
-// cell crossing for every lane that is inside a traversal, whatever kind of
-// traversal it is (absorption deposit, forced-interaction search, or
-// peel-off line of sight).  Lanes that just finished a traversal handle their
-// event (launch, scattering, peel-off tally) and rejoin the stepping loop.
+// Photon-packet life cycle on the GPU, plain FP64 form: one packet per
+// thread, written as a per-thread state machine so that every iteration of
+// the main loop does one cell crossing for every lane that is inside a
+// traversal, whatever kind of traversal it is (absorption deposit,
+// forced-interaction search, or peel-off line of sight).  Lanes that just
+// finished a traversal handle their event (launch, scattering, peel-off
+// tally) and rejoin the stepping loop.  Every quantity is FP64.  The mixed
+// form lives in trace_mixed.cu.
 //
 // Method (arXiv:1705.04702): Sect. 3.2 (stellar emission phase: packets per
 // wavelength, Monte Carlo launch / interaction sampling, peel-off to every
@@ -16,24 +18,12 @@
 #include <math.h>
 
 #include "skirt_internal.cuh"
+#include "trace_device.cuh"
 
 namespace skirt {
 namespace {
 
-enum { M_NONE = 0, M_DEPOSIT = 1, M_LOCATE = 2, M_PEEL = 3 };
-enum {
-    ST_NEW = 0,
-    ST_START_DEP,
-    ST_DEPOSIT_DONE,
-    ST_LOCATE_DONE,
-    ST_PEEL_DONE,
-    ST_AFTER_SCATTER,
-    ST_END_PACKET,
-};
-
-// Precision policy.  R is the type of positions, directions, path lengths
-// and per-cell optical depths; cumulative optical depth, luminosities and
-// tallies are double in both forms.
+// Arithmetic policy of the plain form (R = double throughout).
 template <typename R> struct P;
 
 template <> struct P<double> {
@@ -54,77 +44,6 @@ template <> struct P<double> {
     static __device__ __forceinline__ double inv_dpx(const InstrDev& I) { return I.inv_dpx; }
     static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
 };
-
-template <> struct P<float> {
-    static __device__ __forceinline__ float kr(const TraceArgs& a, int m) { return __ldg(a.kr32 + m); }
-    static __device__ __forceinline__ float logr(float x) { return logf(x); }
-    static __device__ __forceinline__ float sqrtr(float x) { return sqrtf(x); }
-    static __device__ __forceinline__ float floorr(float x) { return floorf(x); }
-    static __device__ __forceinline__ void sincospi2(float u, float* s, float* c) { sincospif(2.0f * u, s, c); }
-    static __device__ __forceinline__ float u(uint32_t x) { return u01f(x); }
-    // the attenuation factor is evaluated in FP32 from the FP64 running
-    // optical depth; its relative error is ~tau * 6e-8
-    static __device__ __forceinline__ double dep_factor(double tau_prev, float dtau) {
-        return (double)(expf(-(float)tau_prev) * (-expm1f(-dtau)));
-    }
-    static __device__ __forceinline__ float kobs(const InstrDev& I, int a) { return I.kobs_f[a]; }
-    static __device__ __forceinline__ float e1(const InstrDev& I, int a) { return I.e1_f[a]; }
-    static __device__ __forceinline__ float e2(const InstrDev& I, int a) { return I.e2_f[a]; }
-    static __device__ __forceinline__ float half_fov(const InstrDev& I) { return I.half_fov_f; }
-    static __device__ __forceinline__ float inv_dpx(const InstrDev& I) { return I.inv_dpx_f; }
-    static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
-};
-
-// Warp-aggregated FP64 reduction: lanes of the converged group that target
-// the same address combine their values through shared memory and one lane
-// issues a single red.global.add.f64.
-__device__ __forceinline__ void red_agg(double* addr, double v, double* wbuf)
-{
-    const unsigned active = __activemask();
-    const unsigned peers = __match_any_sync(active, (unsigned long long)addr);
-    const int lane = threadIdx.x & 31;
-    if (peers == (1u << lane)) {
-        atomicAdd(addr, v);
-        return;
-    }
-    wbuf[lane] = v;
-    __syncwarp(peers);
-    if (lane == __ffs(peers) - 1) {
-        double s = 0.0;
-        unsigned p = peers;
-        while (p) {
-            s += wbuf[__ffs(p) - 1];
-            p &= p - 1;
-        }
-        atomicAdd(addr, s);
-    }
-    __syncwarp(peers);
-}
-
-template <typename R>
-__device__ __forceinline__ R hg_phase(R g, R mu)
-{
-    R den = (R)1 + g * g - (R)2 * g * mu;
-    return ((R)1 - g * g) / (den * P<R>::sqrtr(den));
-}
-
-template <typename R>
-__device__ __forceinline__ R hg_mu(R g, R u)
-{
-    if (fabs(g) < (R)1e-6) return (R)2 * u - (R)1;
-    R t = ((R)1 - g * g) / ((R)1 - g + (R)2 * g * u);
-    R mu = ((R)1 + g * g - t * t) / ((R)2 * g);
-    return fmin(fmax(mu, (R)-1), (R)1);
-}
-
-template <typename R>
-__device__ __forceinline__ int cell_index(R x, R lo, R d, int n)
-{
-    R f = P<R>::floorr((x - lo) / d);
-    if (f < (R)0) return 0;
-    if (f > (R)(n - 1)) return n - 1;
-    return (int)f;
-}
 
 template <typename R>
 __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A)
@@ -487,19 +406,7 @@ __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A)
                 const R mu = hg_mu<R>(gg, P<R>::u(r.y));
                 R sp, cp;
                 P<R>::sincospi2(P<R>::u(r.z), &sp, &cp);
-                const R st = P<R>::sqrtr(fmax((R)1 - mu * mu, (R)0));
-                R n0, n1, n2;
-                if (fabs(k2) > (R)0.99999) {
-                    n0 = st * cp;
-                    n1 = st * sp;
-                    n2 = (k2 > (R)0) ? mu : -mu;
-                } else {
-                    const R s = P<R>::sqrtr((R)1 - k2 * k2);
-                    n0 = st * (k0 * k2 * cp - k1 * sp) / s + k0 * mu;
-                    n1 = st * (k1 * k2 * cp + k0 * sp) / s + k1 * mu;
-                    n2 = -st * cp * s + k2 * mu;
-                }
-                k0 = n0; k1 = n1; k2 = n2;
+                hg_rotate<R>(k0, k1, k2, mu, sp, cp);
                 stage = ST_START_DEP;
             }
             continue;
@@ -573,18 +480,17 @@ size_t trace_smem_bytes(int ninstr, int block) { return sizeof(InstrDev) * (size
 
 cudaError_t launch_trace(const TraceArgs& a, int precision, int block, int grid, cudaStream_t s)
 {
+    if (precision == SKIRT_PREC_MIXED) return launch_trace_mixed(a, block, grid, s);
     const size_t smem = trace_smem_bytes(a.ninstr, block);
-    if (precision == SKIRT_PREC_FP64) trace_kernel<double><<<grid, block, smem, s>>>(a);
-    else trace_kernel<float><<<grid, block, smem, s>>>(a);
+    trace_kernel<double><<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t trace_occupancy(int precision, int block, int* blocks_per_sm)
 {
+    if (precision == SKIRT_PREC_MIXED) return trace_mixed_occupancy(block, blocks_per_sm);
     const size_t smem = trace_smem_bytes(16, block);
-    if (precision == SKIRT_PREC_FP64)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<double>, block, smem);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<float>, block, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<double>, block, smem);
 }
 
 cudaError_t launch_sed_finalize(const double* images, const double* oof, double* sed, int ninstr,

@@ -43,7 +43,8 @@ class skirt_trace_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("schedule", ctypes.c_int), ("w_min", ctypes.c_double),
                 ("max_events", ctypes.c_int), ("peel", ctypes.c_int), ("accumulate", ctypes.c_int),
                 ("block", ctypes.c_int), ("chunk", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("phase", ctypes.c_uint32), ("nrec", ctypes.c_int),
+                ("use_graph", ctypes.c_int), ("step_min", ctypes.c_int), ("phase", ctypes.c_uint32),
+                ("nrec", ctypes.c_int),
                 ("records", ctypes.c_void_p)]
 
 

@@ -51,6 +51,10 @@ def _check(S, oracle_lib, prob, precision, nrec=0, **kw):
     tot = g["ledger"]
     closure = abs(tot["emitted"] - tot["absorbed"] - tot["escaped"] - tot["residual"]) / max(tot["emitted"], 1e-300)
     assert closure < (1e-12 if fp64 else 1e-6), closure
+    # the table holds what the packets deposited (per-event bookkeeping in the
+    # ledger, per-cell reductions in the table)
+    table = float(g["absorbed"].sum())
+    assert table == pytest.approx(tot["absorbed"], rel=1e-12 if fp64 else 1e-6)
     if fp64:
         assert tot["scatterings"] == r["counters"][0]
     return g, r
@@ -81,7 +85,7 @@ def test_schedules_and_launch_shapes_give_identical_histories(S, schedule):
     schedule, block size and refill chunk gives bit-identical records."""
     prob = W.torus_problem(n=32, nlambda=5, packet_scale=1e-4, npx=32)
     base = S.run_problem(prob, precision=S.PREC_MIXED, schedule=S.SCHED_PERSISTENT, nrec=500)
-    for block, chunk in ((64, 1), (256, 3), (512, 16)):
+    for block, chunk in ((64, 1), (128, 3), (256, 16)):
         other = S.run_problem(prob, precision=S.PREC_MIXED, schedule=schedule, nrec=500, block=block, chunk=chunk)
         assert np.array_equal(_np(base["records"]), _np(other["records"]))
         compare_tally(_np(other["absorbed"]), _np(base["absorbed"]), 1e-12)
