@@ -21,9 +21,14 @@
 //    against the remainder (tau_int - FP64 total).  The deposit factor
 //    e^{-tau_prev}(1 - e^{-dtau}) is evaluated in FP32 and widened once for
 //    the FP64 reduction.
-//  * The interaction cell found by the search (a decision taken on the
-//    optical depth) is carried into the next traversals instead of being
-//    recomputed from the rounded FP32 position.
+//  * The packet position is kept in FP64 (touched only at events).  Each
+//    traversal takes the distance to its first faces in FP64 and the later
+//    faces in FP32.  An interaction point is placed on the exact plane of the
+//    face through which its cell was entered plus the in-cell distance, so
+//    that points deep inside optically thick cells (where the interaction
+//    sits ~1/(kappa rho) from the face) keep their relative precision.  The
+//    interaction cell found by the search (a decision taken on the optical
+//    depth) is carried into the next traversals.
 //  * Per event, the escaped / absorbed / scattered split uses one
 //    om = 1 - e^{-tau_path}, so escaped + absorbed + scattered = L to FP64
 //    rounding, and the per-packet absorbed luminosity is L (1 - albedo) om.
@@ -46,6 +51,7 @@ constexpr int ROUND = 4;    // cell crossings per stepping round between warp vo
 struct Cold {
     double L0[MAXB], p_esc[MAXB], p_abs[MAXB], p_res[MAXB], p_peel[MAXB];
     double tau_t[MAXB], om[MAXB], peel_w[MAXB];
+    double xd0[MAXB], xd1[MAXB], xd2[MAXB];  // packet position (FP64)
     double l_emit[MAXB], l_abs[MAXB], l_esc[MAXB], l_res[MAXB];
     unsigned long long q[MAXB], q_end[MAXB];
     unsigned long long c_dep[MAXB], c_loc[MAXB], c_peel[MAXB], c_scat[MAXB];
@@ -77,6 +83,7 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
     const int nx = A.nx, ny = A.ny, nz = A.nz;
     const float lo0 = (float)A.lo[0], lo1 = (float)A.lo[1], lo2 = (float)A.lo[2];
     const float d0 = (float)A.d[0], d1 = (float)A.d[1], d2 = (float)A.d[2];
+    const double Dlo0 = A.lo[0], Dlo1 = A.lo[1], Dlo2 = A.lo[2], Dd0 = A.d[0], Dd1 = A.d[1], Dd2 = A.d[2];
     const float INF = __int_as_float(0x7f800000);
     const float* __restrict__ kr = A.kr32;
     double* __restrict__ absorbed = A.absorbed;
@@ -98,34 +105,39 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
     bool alive = true;
     int lam = 0;
     float krs = 0.f, gg = 0.f;
-    float x0 = 0.f, x1 = 0.f, x2 = 0.f, k0 = 0.f, k1 = 0.f, k2 = 0.f;
+    float x0 = 0.f, x1 = 0.f, x2 = 0.f, k0 = 0.f, k1 = 0.f, k2 = 0.f;  // x: FP32 copy of the position
+    int last_axis = -1;  // axis of the face through which the current cell was entered
     double L = 0.0;
     bool have_pc = false;
     int pc0 = 0, pc1 = 0, pc2 = 0;
 
     auto begin = [&](int m, float vx, float vy, float vz) {
         mode = m;
+        const double X0 = C.xd0[t], X1 = C.xd1[t], X2 = C.xd2[t];
         if (have_pc) {
             c0 = pc0; c1 = pc1; c2 = pc2;
         } else {
-            c0 = cell_index<float>(x0, lo0, d0, nx);
-            c1 = cell_index<float>(x1, lo1, d1, ny);
-            c2 = cell_index<float>(x2, lo2, d2, nz);
+            c0 = cell_index<double>(X0, Dlo0, Dd0, nx);
+            c1 = cell_index<double>(X1, Dlo1, Dd1, ny);
+            c2 = cell_index<double>(X2, Dlo2, Dd2, nz);
         }
+        x0 = (float)X0; x1 = (float)X1; x2 = (float)X2;
         s0 = vx > 0.f ? 1 : (vx < 0.f ? -1 : 0);
         s1 = vy > 0.f ? 1 : (vy < 0.f ? -1 : 0);
         s2 = vz > 0.f ? 1 : (vz < 0.f ? -1 : 0);
         iv0 = s0 ? 1.f / vx : 0.f;
         iv1 = s1 ? 1.f / vy : 0.f;
         iv2 = s2 ? 1.f / vz : 0.f;
-        tn0 = s0 ? (lo0 + (float)(c0 + (s0 > 0)) * d0 - x0) * iv0 : INF;
-        tn1 = s1 ? (lo1 + (float)(c1 + (s1 > 0)) * d1 - x1) * iv1 : INF;
-        tn2 = s2 ? (lo2 + (float)(c2 + (s2 > 0)) * d2 - x2) * iv2 : INF;
+        // first faces in FP64: a start point close to a face keeps its short first segment
+        tn0 = s0 ? (float)((Dlo0 + (double)(c0 + (s0 > 0)) * Dd0 - X0) * (double)iv0) : INF;
+        tn1 = s1 ? (float)((Dlo1 + (double)(c1 + (s1 > 0)) * Dd1 - X1) * (double)iv1) : INF;
+        tn2 = s2 ? (float)((Dlo2 + (double)(c2 + (s2 > 0)) * Dd2 - X2) * (double)iv2) : INF;
         tcur = 0.f;
         tau_hi = 0.0;
         tau_lo = tau_hi_f = 0.f;
         nflush = FLUSH;
         nsteps = 0;
+        last_axis = -1;
     };
 
     // one cell crossing of the current traversal
@@ -141,7 +153,7 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
         if (mode == M_LOCATE) {
             if (krl > 0.f) {
                 if (tau_lo + dtau >= rem_f) {
-                    s_found = tcur + (rem_f - tau_lo) / krl;
+                    s_found = (rem_f - tau_lo) / krl;  // distance inside the current cell
                     found = true;
                     done = true;
                 } else {
@@ -170,6 +182,7 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                 if (axis == 0) { c0 = cn; tn0 = tnew; }
                 else if (axis == 1) { c1 = cn; tn1 = tnew; }
                 else { c2 = cn; tn2 = tnew; }
+                last_axis = axis;
             }
         }
         if (--nflush == 0 || done) {
@@ -315,6 +328,16 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                 } else {
                     x0 = (float)A.src_pos[0]; x1 = (float)A.src_pos[1]; x2 = (float)A.src_pos[2];
                 }
+                if (A.src_kind == SKIRT_SRC_POINT || A.src_kind == SKIRT_SRC_BEAM) {
+                    C.xd0[t] = A.src_pos[0]; C.xd1[t] = A.src_pos[1]; C.xd2[t] = A.src_pos[2];
+                } else if (A.src_kind == SKIRT_SRC_DUST) {
+                    const uint4 r = draw(0u, 0u);
+                    C.xd0[t] = Dlo0 + ((double)pc0 + (double)u01f(r.y)) * Dd0;
+                    C.xd1[t] = Dlo1 + ((double)pc1 + (double)u01f(r.z)) * Dd1;
+                    C.xd2[t] = Dlo2 + ((double)pc2 + (double)u01f(r.w)) * Dd2;
+                } else {
+                    C.xd0[t] = x0; C.xd1[t] = x1; C.xd2[t] = x2;
+                }
                 if (isotropic) {
                     const uint4 r = draw(0u, 1u);
                     const float mu = 2.f * u01f(r.x) - 1.f;
@@ -346,8 +369,11 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
             if (stage == ST_DEPOSIT_DONE) {
                 C.c_dep[t] += nsteps;
                 const double tau_path = tau_hi;
-                const float om_f = -expm1f(-(float)tau_path);
-                const double om = (double)om_f;
+                // om = 1 - e^{-tau_path}: from expm1 for small tau, from 1 - exp for large
+                // tau, so that both om and 1 - om keep FP32 relative precision
+                const float tf = (float)tau_path;
+                const double om = tf < 0.6931472f ? (double)(-expm1f(-tf)) : 1.0 - (double)expf(-tf);
+                const float om_f = (float)om;
                 C.p_esc[t] += L * (1.0 - om);
                 C.p_abs[t] += L * (1.0 - (double)C.alb[t]) * om;
                 if (!(tau_path > 0.0)) {
@@ -372,10 +398,23 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
 
             if (stage == ST_LOCATE_DONE) {
                 C.c_loc[t] += nsteps;
-                const float s = found ? s_found : last_dusty_end;
-                x0 += s * k0;
-                x1 += s * k1;
-                x2 += s * k2;
+                double X0 = C.xd0[t], X1 = C.xd1[t], X2 = C.xd2[t];
+                const double K0 = k0, K1 = k1, K2 = k2;
+                if (found && last_axis >= 0) {
+                    // entry point of the interaction cell, snapped onto the exact face plane
+                    const double te = (double)tcur;
+                    X0 += te * K0; X1 += te * K1; X2 += te * K2;
+                    if (last_axis == 0) X0 = Dlo0 + (double)(c0 + (s0 < 0)) * Dd0;
+                    else if (last_axis == 1) X1 = Dlo1 + (double)(c1 + (s1 < 0)) * Dd1;
+                    else X2 = Dlo2 + (double)(c2 + (s2 < 0)) * Dd2;
+                    const double si = (double)s_found;
+                    X0 += si * K0; X1 += si * K1; X2 += si * K2;
+                } else {
+                    const double s = found ? (double)s_found : (double)last_dusty_end;
+                    X0 += s * K0; X1 += s * K1; X2 += s * K2;
+                }
+                C.xd0[t] = X0; C.xd1[t] = X1; C.xd2[t] = X2;
+                x0 = (float)X0; x1 = (float)X1; x2 = (float)X2;
                 have_pc = found;
                 if (found) { pc0 = c0; pc1 = c1; pc2 = c2; }
                 L = L * (double)C.alb[t] * C.om[t];
@@ -400,11 +439,12 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                 if (w > 0.0) {
                     const double flux = w * (double)expf(-(float)tau_hi) * I.flux_norm;
                     C.p_peel[t] += flux;
-                    const float a = x0 * I.e1_f[0] + x1 * I.e1_f[1] + x2 * I.e1_f[2];
-                    const float b = x0 * I.e2_f[0] + x1 * I.e2_f[1] + x2 * I.e2_f[2];
-                    const float fa = floorf((a + I.half_fov_f) * I.inv_dpx_f);
-                    const float fb = floorf((b + I.half_fov_f) * I.inv_dpx_f);
-                    if (fa >= 0.f && fa < (float)I.npx && fb >= 0.f && fb < (float)I.npx) {
+                    const double X0 = C.xd0[t], X1 = C.xd1[t], X2 = C.xd2[t];
+                    const double a = X0 * I.e1[0] + X1 * I.e1[1] + X2 * I.e1[2];
+                    const double b = X0 * I.e2[0] + X1 * I.e2[1] + X2 * I.e2[2];
+                    const double fa = floor((a + I.half_fov) * I.inv_dpx);
+                    const double fb = floor((b + I.half_fov) * I.inv_dpx);
+                    if (fa >= 0.0 && fa < (double)I.npx && fb >= 0.0 && fb < (double)I.npx) {
                         const long long pix = (long long)fb * I.npx + (long long)fa;
                         red_agg(A.images + I.img_off + pix * NL + lam, flux, wbuf);
                     } else {
@@ -452,9 +492,9 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                 rec[2] = pa;
                 rec[3] = pr;
                 rec[4] = pp;
-                rec[5] = (double)x0;
-                rec[6] = (double)x1;
-                rec[7] = (double)x2;
+                rec[5] = C.xd0[t];
+                rec[6] = C.xd1[t];
+                rec[7] = C.xd2[t];
             }
             stage = ST_NEW;
         }
