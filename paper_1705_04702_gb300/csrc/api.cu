@@ -65,7 +65,7 @@ constexpr double kPi = 3.14159265358979323846;
 namespace {
 
 struct Layout {
-    size_t kscale, albedo, g, L0, offsets, ins, ledger, oof, counters, err, queue, total;
+    size_t kscale, albedo, g, L0, kscale_f, albedo_f, g_f, L0_f, offsets, ins, ledger, oof, counters, err, queue, total;
     size_t zero_begin, zero_bytes;  // accumulators zeroed every call
 };
 
@@ -82,6 +82,10 @@ Layout make_layout(int NL, int ninstr)
     l.albedo = take(sizeof(double) * NL);
     l.g = take(sizeof(double) * NL);
     l.L0 = take(sizeof(double) * NL);
+    l.kscale_f = take(sizeof(float) * NL);
+    l.albedo_f = take(sizeof(float) * NL);
+    l.g_f = take(sizeof(float) * NL);
+    l.L0_f = take(sizeof(float) * NL);
     l.offsets = take(sizeof(unsigned long long) * (NL + 1));
     l.ins = take(sizeof(InstrDev) * (ninstr > 0 ? ninstr : 1));
     l.ledger = take(sizeof(double) * 4 * NL);
@@ -114,6 +118,7 @@ void fill_instrument(const skirt_instrument& s, InstrDev& d, long long img_off)
     d.half_fov_f = (float)d.half_fov;
     d.inv_dpx_f = (float)d.inv_dpx;
     d.flux_norm = 1.0 / (4.0 * kPi * s.distance * s.distance);
+    d.flux_norm_f = (float)d.flux_norm;
     d.npx = s.npx;
     d.img_off = img_off;
 }
@@ -174,6 +179,23 @@ extern "C" int skirt_grid_create(skirt_grid_t* out, int nx, int ny, int nz, cons
     std::memcpy(g->bbox, bbox, sizeof g->bbox);
     if ((e = cudaMalloc(&g->kr32, sizeof(float) * ncell)) != cudaSuccess) return bail(fail(SKIRT_ERR_OOM, "kr32: %s", cudaGetErrorString(e)));
     if ((e = cudaMalloc(&g->kr64, sizeof(double) * ncell)) != cudaSuccess) return bail(fail(SKIRT_ERR_OOM, "kr64: %s", cudaGetErrorString(e)));
+    {
+        // face planes lo + k d (k < n) and the upper bound, split into (hi, lo) FP32 pairs
+        std::vector<float2> f;
+        const int nn[3] = {nx, ny, nz};
+        for (int a = 0; a < 3; ++a) {
+            const double lo = bbox[2 * a], hi = bbox[2 * a + 1], d = (hi - lo) / nn[a];
+            for (int k = 0; k <= nn[a]; ++k) {
+                const double v = k < nn[a] ? lo + (double)k * d : hi;
+                const float h = (float)v;
+                f.push_back(make_float2(h, (float)(v - (double)h)));
+            }
+        }
+        if ((e = cudaMalloc(&g->faces, sizeof(float2) * f.size())) != cudaSuccess)
+            return bail(fail(SKIRT_ERR_OOM, "faces: %s", cudaGetErrorString(e)));
+        if ((e = cudaMemcpy(g->faces, f.data(), sizeof(float2) * f.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(fail(SKIRT_ERR_CUDA, "faces: %s", cudaGetErrorString(e)));
+    }
     if ((e = cudaEventCreate(&g->ev0)) != cudaSuccess || (e = cudaEventCreate(&g->ev1)) != cudaSuccess)
         return bail(fail(SKIRT_ERR_CUDA, "event: %s", cudaGetErrorString(e)));
     if ((e = cudaStreamCreateWithFlags(&g->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
@@ -198,6 +220,7 @@ extern "C" int skirt_grid_destroy(skirt_grid_t g)
     if (g->gexec) cudaGraphExecDestroy(g->gexec);
     if (g->kr32) cudaFree(g->kr32);
     if (g->kr64) cudaFree(g->kr64);
+    if (g->faces) cudaFree(g->faces);
     g->scratch.release();
     g->stage.release();
     g->cdf.release();
@@ -325,11 +348,19 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
     double* h_al = (double*)(hp + L.albedo);
     double* h_g = (double*)(hp + L.g);
     double* h_L0 = (double*)(hp + L.L0);
+    float* h_ksf = (float*)(hp + L.kscale_f);
+    float* h_alf = (float*)(hp + L.albedo_f);
+    float* h_gf = (float*)(hp + L.g_f);
+    float* h_L0f = (float*)(hp + L.L0_f);
     for (int j = 0; j < NL; ++j) {
         h_ks[j] = wl->kscale[j];
         h_al[j] = wl->albedo[j];
         h_g[j] = wl->g[j];
         h_L0[j] = npk[j] ? wl->lsrc[j] / (double)npk[j] : 0.0;
+        h_ksf[j] = (float)h_ks[j];
+        h_alf[j] = (float)h_al[j];
+        h_gf[j] = (float)h_g[j];
+        h_L0f[j] = (float)h_L0[j];
     }
     std::memcpy(hp + L.offsets, P.offsets.data(), sizeof(unsigned long long) * (NL + 1));
     InstrDev* h_ins = (InstrDev*)(hp + L.ins);
@@ -395,6 +426,17 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
     A.albedo = (const double*)(dp + L.albedo);
     A.g = (const double*)(dp + L.g);
     A.L0 = (const double*)(dp + L.L0);
+    A.kscale_f = (const float*)(dp + L.kscale_f);
+    A.albedo_f = (const float*)(dp + L.albedo_f);
+    A.g_f = (const float*)(dp + L.g_f);
+    A.L0_f = (const float*)(dp + L.L0_f);
+    A.faces = g->faces;
+    for (int a = 0; a < 3; ++a) {
+        const float hi = (float)src->pos[a];
+        A.src_df[a] = make_float2(hi, (float)(src->pos[a] - (double)hi));
+        A.src_dir_f[a] = (float)src->dir[a];
+        A.hi_f[a] = (float)g->bbox[2 * a + 1];
+    }
     A.offsets = (const unsigned long long*)(dp + L.offsets);
     A.total = P.total;
     A.src_kind = src->kind;
@@ -416,6 +458,7 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
     A.nrec = opts->nrec;
     A.records = d_rec;
     A.w_min = opts->w_min > 0 ? opts->w_min : 1e-4;
+    A.w_min_f = (float)A.w_min;
     A.max_events = opts->max_events > 0 ? opts->max_events : 10000;
     A.peel = peel ? 1 : 0;
     A.key0 = (uint32_t)(seed & 0xffffffffu);

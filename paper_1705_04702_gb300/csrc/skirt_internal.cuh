@@ -39,7 +39,7 @@ struct InstrDev {
     double kobs[3], e1[3], e2[3];
     double half_fov, inv_dpx, flux_norm;
     float kobs_f[3], e1_f[3], e2_f[3];
-    float half_fov_f, inv_dpx_f;
+    float half_fov_f, inv_dpx_f, flux_norm_f;
     int npx;
     long long img_off;  // element offset of this instrument in the images array
 };
@@ -56,6 +56,15 @@ struct TraceArgs {
     const double* albedo;
     const double* g;
     const double* L0;                      // luminosity per packet at each wavelength
+    const float* kscale_f;                 // FP32 copies of the four tables (mixed form)
+    const float* albedo_f;
+    const float* g_f;
+    const float* L0_f;
+    const float2* faces;                   // face planes as (hi, lo) FP32 pairs: x [nx+1], y [ny+1], z [nz+1]
+    float2 src_df[3];                      // source position as (hi, lo) FP32 pairs
+    float src_dir_f[3];
+    float hi_f[3];
+    float w_min_f;
     const unsigned long long* offsets;     // [nlambda + 1] prefix sums of packet counts
     unsigned long long total;
     int src_kind;
@@ -160,6 +169,7 @@ struct skirt_grid_s {
     double bbox[6] = {0, 0, 0, 0, 0, 0};
     float* kr32 = nullptr;
     double* kr64 = nullptr;
+    float2* faces = nullptr;  // exact face planes as (hi, lo) FP32 pairs, x then y then z
     skirt::DevBuf scratch;  // per-call tables, accumulators, work queue
     skirt::DevBuf stage;    // device images of host outputs
     skirt::DevBuf cdf;      // dust source: [nlambda][ncell] cumulative distributions

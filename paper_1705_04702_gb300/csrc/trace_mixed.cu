@@ -1,39 +1,37 @@
-// Photon-packet life cycle on the GPU, mixed form: FP32 positions,
-// directions, cell traversal and phase-function sampling; FP64 cumulative
-// optical depth, packet luminosity and tallies.
+// Photon-packet life cycle on the GPU, mixed form: FP32 cell traversal,
+// directions, phase-function sampling and packet luminosity; FP64 cumulative
+// optical depth, tallies and energy ledger.
 //
 // Same method as the FP64 form (Sect. 3.2 stellar emission phase: launch,
 // peel-off towards every instrument, continuous absorption into the
 // [cell, wavelength] table, forced scattering, life until a negligible
 // luminosity is left; Sect. 1 for the techniques; Sect. 5.2 for the table
-// layout and lock-free additions), organised for a GPU whose FP64 and
-// FP32<->FP64 conversion rates are ~1/64 of its FP32 rate:
+// layout and lock-free additions), organised for a GPU whose FP64 unit
+// retires a warp instruction only every few dozen cycles per sub-partition:
+// every FP64 or FP32<->FP64 conversion instruction a warp issues, even with
+// one lane active, costs that much.  So:
 //
 //  * Warp-coherent stepping.  All lanes of a warp step one cell per round
 //    whatever traversal they are in (deposit, forced-interaction search,
 //    peel-off line of sight).  A lane whose traversal ended idles until fewer
 //    than step_min lanes are still stepping; then the idle lanes handle
-//    their events (launch, scattering, peel-off tally) together.  This keeps
-//    the long, branchy event code from running with one lane active.
-//  * No FP64 per cell crossing.  The optical depth of each crossing is FP32;
-//    up to FLUSH of them are summed in FP32 and the partial sum is added to
-//    an FP64 running total.  The forced-interaction search compares in FP32
-//    against the remainder (tau_int - FP64 total).  The deposit factor
-//    e^{-tau_prev}(1 - e^{-dtau}) is evaluated in FP32 and widened once for
-//    the FP64 reduction.
-//  * The packet position is kept in FP64 (touched only at events).  Each
-//    traversal takes the distance to its first faces in FP64 and the later
-//    faces in FP32.  An interaction point is placed on the exact plane of the
-//    face through which its cell was entered plus the in-cell distance, so
-//    that points deep inside optically thick cells (where the interaction
-//    sits ~1/(kappa rho) from the face) keep their relative precision.  The
-//    interaction cell found by the search (a decision taken on the optical
-//    depth) is carried into the next traversals.
-//  * Per event, the escaped / absorbed / scattered split uses one
-//    om = 1 - e^{-tau_path}, so escaped + absorbed + scattered = L to FP64
-//    rounding, and the per-packet absorbed luminosity is L (1 - albedo) om.
-//  * Cold per-thread state (bookkeeping touched only at events) lives in
-//    shared memory, leaving registers for the stepping state.
+//    their events (launch, scattering, peel-off tally) together.
+//  * Per cell crossing only FP32 arithmetic.  Optical depths of crossings are
+//    summed in FP32 and, every FLUSH warp rounds, the partial sums of all
+//    lanes are added to their FP64 running totals at once (one FP64
+//    instruction per warp).  The forced-interaction search compares in FP32
+//    against the remainder tau_int - (FP64 total).  Deposits are formed in
+//    FP32 and widened to FP64 by integer bit operations for the reduction.
+//  * Positions are double-float pairs (hi + lo, ~48 bits).  Face planes come
+//    from exact per-grid tables; the distance from a start point to its first
+//    faces and the snapping of an interaction point onto the plane through
+//    which its cell was entered keep full relative precision for points deep
+//    inside optically thick cells (~1/(kappa rho) from a face).  The
+//    interaction cell found by the search is carried into the next
+//    traversals.
+//  * Per event, escaped / absorbed / scattered come from one
+//    om = 1 - e^{-tau_path}, so they add up to the packet luminosity.
+//  * Per-thread state used only at events lives in shared memory.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -43,19 +41,60 @@
 namespace skirt {
 namespace {
 
-constexpr int MAXB = 256;   // threads per block of the mixed kernel (upper bound)
-constexpr int FLUSH = 16;   // FP32 partial optical depths per FP64 accumulation
-constexpr int ROUND = 4;    // cell crossings per stepping round between warp votes
+constexpr int MAXB = 256;  // threads per block of the mixed kernel (upper bound)
+constexpr int FLUSH = 32;  // warp rounds between FP64 accumulations of the optical depth
+constexpr int ROUND = 4;   // cell crossings per stepping round between warp votes
+
+// FP32 -> FP64 and FP64 -> FP32 by IEEE-754 field manipulation on the
+// integer pipe.  f2d is exact for normal floats (zero and FP32 subnormals map
+// to zero); d2f truncates towards zero (FP64 values outside the FP32 range
+// saturate to zero / infinity).
+__device__ __forceinline__ double f2d(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned ex = (u >> 23) & 0xFFu;
+    const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
+                                    ((unsigned long long)(ex + 896u) << 52) |
+                                    ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return ex ? __longlong_as_double((long long)bits) : 0.0;
+}
+
+__device__ __forceinline__ float d2f(double d)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    const int ex = (int)((u >> 52) & 0x7FF) - 896;
+    const unsigned sign = (unsigned)(u >> 63) << 31;
+    if (ex <= 0) return __uint_as_float(sign);
+    if (ex >= 255) return __uint_as_float(sign | 0x7F800000u);
+    return __uint_as_float(sign | ((unsigned)ex << 23) | (unsigned)((u >> 29) & 0x7FFFFFu));
+}
+
+// Double-float arithmetic (Knuth / Dekker error-free transformations), with
+// round-to-nearest intrinsics so that nothing is contracted into an FMA.
+__device__ __forceinline__ void df_add_prod(float& hi, float& lo, float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    const float pe = fmaf(a, b, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb)), __fadd_rn(lo, pe));
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+__device__ __forceinline__ float df_diff(float2 f, float xh, float xl)
+{
+    return __fadd_rn(__fsub_rn(f.x, xh), __fsub_rn(f.y, xl));
+}
 
 // Per-thread state used only at events, struct of arrays in shared memory.
 struct Cold {
-    double L0[MAXB], p_esc[MAXB], p_abs[MAXB], p_res[MAXB], p_peel[MAXB];
-    double tau_t[MAXB], om[MAXB], peel_w[MAXB];
-    double xd0[MAXB], xd1[MAXB], xd2[MAXB];  // packet position (FP64)
+    double tau_t[MAXB];
     double l_emit[MAXB], l_abs[MAXB], l_esc[MAXB], l_res[MAXB];
     unsigned long long q[MAXB], q_end[MAXB];
     unsigned long long c_dep[MAXB], c_loc[MAXB], c_peel[MAXB], c_scat[MAXB];
-    float alb[MAXB];
+    float L0[MAXB], p_esc[MAXB], p_abs[MAXB], p_res[MAXB], p_peel[MAXB], om[MAXB], peel_w[MAXB], alb[MAXB];
+    float xl0[MAXB], xl1[MAXB], xl2[MAXB];  // low words of the double-float position
     int lam[MAXB], led_lam[MAXB], nscat[MAXB], peel_i[MAXB], after_peel[MAXB], peel_kind[MAXB];
     unsigned pk[MAXB], ev[MAXB], started[MAXB];
 };
@@ -83,9 +122,11 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
     const int nx = A.nx, ny = A.ny, nz = A.nz;
     const float lo0 = (float)A.lo[0], lo1 = (float)A.lo[1], lo2 = (float)A.lo[2];
     const float d0 = (float)A.d[0], d1 = (float)A.d[1], d2 = (float)A.d[2];
-    const double Dlo0 = A.lo[0], Dlo1 = A.lo[1], Dlo2 = A.lo[2], Dd0 = A.d[0], Dd1 = A.d[1], Dd2 = A.d[2];
     const float INF = __int_as_float(0x7f800000);
     const float* __restrict__ kr = A.kr32;
+    const float2* __restrict__ fx = A.faces;
+    const float2* __restrict__ fy = A.faces + (nx + 1);
+    const float2* __restrict__ fz = A.faces + (nx + 1) + (ny + 1);
     double* __restrict__ absorbed = A.absorbed;
     const int step_min = A.step_min > 0 ? A.step_min : 16;
 
@@ -95,47 +136,52 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
     float iv0 = 0.f, iv1 = 0.f, iv2 = 0.f, tn0 = 0.f, tn1 = 0.f, tn2 = 0.f, tcur = 0.f;
     double tau_hi = 0.0;
     float tau_lo = 0.f, tau_hi_f = 0.f, rem_f = 0.f;
-    int nflush = FLUSH;
     unsigned nsteps = 0;
     float labs_f = 0.f;
     float s_found = 0.f, last_dusty_end = 0.f;
     bool found = false;
+    int last_axis = -1;   // axis of the face through which the current cell was entered
+    unsigned wround = 0;  // warp-uniform round counter
     // ---- packet state (registers)
     int stage = ST_NEW;
     bool alive = true;
     int lam = 0;
-    float krs = 0.f, gg = 0.f;
-    float x0 = 0.f, x1 = 0.f, x2 = 0.f, k0 = 0.f, k1 = 0.f, k2 = 0.f;  // x: FP32 copy of the position
-    int last_axis = -1;  // axis of the face through which the current cell was entered
-    double L = 0.0;
+    float krs = 0.f, gg = 0.f, L = 0.f;
+    float x0 = 0.f, x1 = 0.f, x2 = 0.f;  // position, high words
+    float k0 = 0.f, k1 = 0.f, k2 = 0.f;
     bool have_pc = false;
     int pc0 = 0, pc1 = 0, pc2 = 0;
 
+    auto axis_cell = [&](float xh, float xl, float lo, float d, int n, const float2* f) {
+        int c = (int)fminf(fmaxf(floorf((xh - lo) / d), 0.f), (float)(n - 1));
+        if (c > 0 && df_diff(__ldg(f + c), xh, xl) > 0.f) --c;
+        else if (c < n - 1 && df_diff(__ldg(f + c + 1), xh, xl) <= 0.f) ++c;
+        return c;
+    };
+
     auto begin = [&](int m, float vx, float vy, float vz) {
         mode = m;
-        const double X0 = C.xd0[t], X1 = C.xd1[t], X2 = C.xd2[t];
+        const float l0 = C.xl0[t], l1 = C.xl1[t], l2 = C.xl2[t];
         if (have_pc) {
             c0 = pc0; c1 = pc1; c2 = pc2;
         } else {
-            c0 = cell_index<double>(X0, Dlo0, Dd0, nx);
-            c1 = cell_index<double>(X1, Dlo1, Dd1, ny);
-            c2 = cell_index<double>(X2, Dlo2, Dd2, nz);
+            c0 = axis_cell(x0, l0, lo0, d0, nx, fx);
+            c1 = axis_cell(x1, l1, lo1, d1, ny, fy);
+            c2 = axis_cell(x2, l2, lo2, d2, nz, fz);
         }
-        x0 = (float)X0; x1 = (float)X1; x2 = (float)X2;
         s0 = vx > 0.f ? 1 : (vx < 0.f ? -1 : 0);
         s1 = vy > 0.f ? 1 : (vy < 0.f ? -1 : 0);
         s2 = vz > 0.f ? 1 : (vz < 0.f ? -1 : 0);
         iv0 = s0 ? 1.f / vx : 0.f;
         iv1 = s1 ? 1.f / vy : 0.f;
         iv2 = s2 ? 1.f / vz : 0.f;
-        // first faces in FP64: a start point close to a face keeps its short first segment
-        tn0 = s0 ? (float)((Dlo0 + (double)(c0 + (s0 > 0)) * Dd0 - X0) * (double)iv0) : INF;
-        tn1 = s1 ? (float)((Dlo1 + (double)(c1 + (s1 > 0)) * Dd1 - X1) * (double)iv1) : INF;
-        tn2 = s2 ? (float)((Dlo2 + (double)(c2 + (s2 > 0)) * Dd2 - X2) * (double)iv2) : INF;
+        // first faces from the exact face planes and the double-float position
+        tn0 = s0 ? df_diff(__ldg(fx + c0 + (s0 > 0)), x0, l0) * iv0 : INF;
+        tn1 = s1 ? df_diff(__ldg(fy + c1 + (s1 > 0)), x1, l1) * iv1 : INF;
+        tn2 = s2 ? df_diff(__ldg(fz + c2 + (s2 > 0)), x2, l2) * iv2 : INF;
         tcur = 0.f;
         tau_hi = 0.0;
         tau_lo = tau_hi_f = 0.f;
-        nflush = FLUSH;
         nsteps = 0;
         last_axis = -1;
     };
@@ -162,7 +208,7 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
             }
         } else if (mode == M_DEPOSIT && dtau > 0.f) {
             const float dep = labs_f * expf(-(tau_hi_f + tau_lo)) * (-expm1f(-dtau));
-            if (dep > 0.f) atomicAdd(absorbed + (size_t)m * NL + lam, (double)dep);
+            if (dep >= 1.17549435e-38f) atomicAdd(absorbed + (size_t)m * NL + lam, f2d(dep));
         }
         tau_lo += dtau;
         if (!done) {
@@ -185,14 +231,17 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                 last_axis = axis;
             }
         }
-        if (--nflush == 0 || done) {
-            tau_hi += (double)tau_lo;
-            tau_lo = 0.f;
-            tau_hi_f = (float)tau_hi;
-            nflush = FLUSH;
-            if (mode == M_LOCATE && !done) rem_f = (float)(C.tau_t[t] - tau_hi);
-        }
         if (done) mode = M_NONE;
+    };
+
+    // FP64 accumulation of the lanes' partial optical depths (warp-uniform call)
+    auto flush = [&]() {
+        if (mode != M_NONE) {
+            tau_hi += f2d(tau_lo);
+            tau_lo = 0.f;
+            tau_hi_f = d2f(tau_hi);
+            if (mode == M_LOCATE) rem_f = d2f(C.tau_t[t] - tau_hi);
+        }
     };
 
     auto draw = [&](uint32_t event, uint32_t block) -> uint4 {
@@ -213,15 +262,15 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
 
     auto start_peel = [&](int i) {
         const InstrDev& I = sins[i];
-        double w;
+        float w;
         if (C.peel_kind[t] == 0) {
             w = L;  // isotropic emission: phase factor 1
         } else {
             const float mu = k0 * I.kobs_f[0] + k1 * I.kobs_f[1] + k2 * I.kobs_f[2];
-            w = L * (double)hg_phase<float>(gg, mu);
+            w = L * hg_phase<float>(gg, mu);
         }
         C.peel_w[t] = w;
-        if (w > 0.0) begin(M_PEEL, I.kobs_f[0], I.kobs_f[1], I.kobs_f[2]);
+        if (w > 0.f) begin(M_PEEL, I.kobs_f[0], I.kobs_f[1], I.kobs_f[2]);
         else nsteps = 0;
     };
 
@@ -263,30 +312,34 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                     }
                     ll = a;
                     C.lam[t] = ll;
-                    C.alb[t] = (float)__ldg(A.albedo + ll);
-                    C.L0[t] = __ldg(A.L0 + ll);
+                    C.alb[t] = __ldg(A.albedo_f + ll);
+                    C.L0[t] = __ldg(A.L0_f + ll);
                     if (C.led_lam[t] != ll) {
                         flush_ledger();
                         C.led_lam[t] = ll;
                     }
                 }
                 lam = ll;
-                krs = (float)__ldg(A.kscale + lam);
-                gg = (float)__ldg(A.g + lam);
+                krs = __ldg(A.kscale_f + lam);
+                gg = __ldg(A.g_f + lam);
                 C.pk[t] = (unsigned)(qq - __ldg(A.offsets + lam));
                 L = C.L0[t];
-                C.p_esc[t] = C.p_abs[t] = C.p_res[t] = C.p_peel[t] = 0.0;
+                C.p_esc[t] = C.p_abs[t] = C.p_res[t] = C.p_peel[t] = 0.f;
                 C.ev[t] = 0;
                 C.nscat[t] = 0;
-                C.l_emit[t] += L;
+                C.l_emit[t] += f2d(L);
                 have_pc = false;
+                float l0 = 0.f, l1 = 0.f, l2 = 0.f;
 
                 // ---- launch (Sect. 3.2)
                 bool isotropic = true;
-                if (A.src_kind == SKIRT_SRC_BEAM) {
-                    x0 = (float)A.src_pos[0]; x1 = (float)A.src_pos[1]; x2 = (float)A.src_pos[2];
-                    k0 = (float)A.src_dir[0]; k1 = (float)A.src_dir[1]; k2 = (float)A.src_dir[2];
-                    isotropic = false;
+                if (A.src_kind == SKIRT_SRC_BEAM || A.src_kind == SKIRT_SRC_POINT) {
+                    x0 = A.src_df[0].x; x1 = A.src_df[1].x; x2 = A.src_df[2].x;
+                    l0 = A.src_df[0].y; l1 = A.src_df[1].y; l2 = A.src_df[2].y;
+                    if (A.src_kind == SKIRT_SRC_BEAM) {
+                        k0 = A.src_dir_f[0]; k1 = A.src_dir_f[1]; k2 = A.src_dir_f[2];
+                        isotropic = false;
+                    }
                 } else if (A.src_kind == SKIRT_SRC_DISK) {
                     const float hR = (float)A.h_R, hz = (float)A.h_z;
                     for (uint32_t tries = 0;; ++tries) {
@@ -296,23 +349,22 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                         const float z = (u2 < 0.5f) ? hz * logf(2.f * u2) : -hz * logf(2.f * (1.f - u2));
                         float sp, cp;
                         sincospif(2.f * u3, &sp, &cp);
-                        x0 = (float)A.src_pos[0] + Rr * cp;
-                        x1 = (float)A.src_pos[1] + Rr * sp;
-                        x2 = (float)A.src_pos[2] + z;
-                        if (x0 >= lo0 && x0 <= (float)A.hi[0] && x1 >= lo1 && x1 <= (float)A.hi[1] && x2 >= lo2 &&
-                            x2 <= (float)A.hi[2])
+                        x0 = A.src_df[0].x + Rr * cp;
+                        x1 = A.src_df[1].x + Rr * sp;
+                        x2 = A.src_df[2].x + z;
+                        if (x0 >= lo0 && x0 <= A.hi_f[0] && x1 >= lo1 && x1 <= A.hi_f[1] && x2 >= lo2 && x2 <= A.hi_f[2])
                             break;
                         if (tries + 1 >= 64) {
                             atomicOr(A.err, (unsigned)ERRBIT_SOURCE);
-                            x0 = (float)A.src_pos[0]; x1 = (float)A.src_pos[1]; x2 = (float)A.src_pos[2];
+                            x0 = A.src_df[0].x; x1 = A.src_df[1].x; x2 = A.src_df[2].x;
                             break;
                         }
                     }
-                } else if (A.src_kind == SKIRT_SRC_DUST) {
+                } else {  // SKIRT_SRC_DUST
                     const uint4 r = draw(0u, 0u);
                     const long long ncell = (long long)nx * ny * nz;
                     const double* cdf = A.cdf + (size_t)lam * ncell;
-                    const double u0 = (double)u01f(r.x);
+                    const double u0 = f2d(u01f(r.x));
                     long long a = 0, b = ncell - 1;  // first cell with cdf > u0
                     while (a < b) {
                         const long long mid = (a + b) >> 1;
@@ -321,23 +373,16 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                     pc0 = (int)(a % nx);
                     pc1 = (int)((a / nx) % ny);
                     pc2 = (int)(a / ((long long)nx * ny));
-                    x0 = lo0 + ((float)pc0 + u01f(r.y)) * d0;
-                    x1 = lo1 + ((float)pc1 + u01f(r.z)) * d1;
-                    x2 = lo2 + ((float)pc2 + u01f(r.w)) * d2;
+                    const float2 f0 = __ldg(fx + pc0), f1 = __ldg(fy + pc1), f2 = __ldg(fz + pc2);
+                    x0 = f0.x; l0 = f0.y;
+                    x1 = f1.x; l1 = f1.y;
+                    x2 = f2.x; l2 = f2.y;
+                    df_add_prod(x0, l0, u01f(r.y), d0);
+                    df_add_prod(x1, l1, u01f(r.z), d1);
+                    df_add_prod(x2, l2, u01f(r.w), d2);
                     have_pc = true;
-                } else {
-                    x0 = (float)A.src_pos[0]; x1 = (float)A.src_pos[1]; x2 = (float)A.src_pos[2];
                 }
-                if (A.src_kind == SKIRT_SRC_POINT || A.src_kind == SKIRT_SRC_BEAM) {
-                    C.xd0[t] = A.src_pos[0]; C.xd1[t] = A.src_pos[1]; C.xd2[t] = A.src_pos[2];
-                } else if (A.src_kind == SKIRT_SRC_DUST) {
-                    const uint4 r = draw(0u, 0u);
-                    C.xd0[t] = Dlo0 + ((double)pc0 + (double)u01f(r.y)) * Dd0;
-                    C.xd1[t] = Dlo1 + ((double)pc1 + (double)u01f(r.z)) * Dd1;
-                    C.xd2[t] = Dlo2 + ((double)pc2 + (double)u01f(r.w)) * Dd2;
-                } else {
-                    C.xd0[t] = x0; C.xd1[t] = x1; C.xd2[t] = x2;
-                }
+                C.xl0[t] = l0; C.xl1[t] = l1; C.xl2[t] = l2;
                 if (isotropic) {
                     const uint4 r = draw(0u, 1u);
                     const float mu = 2.f * u01f(r.x) - 1.f;
@@ -360,7 +405,7 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
 
             if (stage == ST_START_DEP) {
                 C.ev[t] += 1;
-                labs_f = (float)(L * (1.0 - (double)C.alb[t]));
+                labs_f = L * (1.f - C.alb[t]);
                 begin(M_DEPOSIT, k0, k1, k2);
                 stage = ST_DEPOSIT_DONE;
                 continue;
@@ -368,17 +413,18 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
 
             if (stage == ST_DEPOSIT_DONE) {
                 C.c_dep[t] += nsteps;
-                const double tau_path = tau_hi;
-                // om = 1 - e^{-tau_path}: from expm1 for small tau, from 1 - exp for large
-                // tau, so that both om and 1 - om keep FP32 relative precision
-                const float tf = (float)tau_path;
-                const double om = tf < 0.6931472f ? (double)(-expm1f(-tf)) : 1.0 - (double)expf(-tf);
-                const float om_f = (float)om;
-                C.p_esc[t] += L * (1.0 - om);
-                C.p_abs[t] += L * (1.0 - (double)C.alb[t]) * om;
+                const double tau_path = tau_hi + f2d(tau_lo);
+                // om = 1 - e^{-tau_path}: from expm1 for small tau, from 1 - exp for
+                // large tau, so that both om and 1 - om keep FP32 relative precision
+                const float tf = d2f(tau_path);
+                float om, E;
+                if (tf < 0.6931472f) { om = -expm1f(-tf); E = 1.f - om; }
+                else { E = expf(-tf); om = 1.f - E; }
+                C.p_esc[t] += L * E;
+                C.p_abs[t] += L * (1.f - C.alb[t]) * om;
                 if (!(tau_path > 0.0)) {
                     if (!(tau_path == 0.0)) atomicOr(A.err, (unsigned)ERRBIT_NONFINITE);
-                    L = 0.0;
+                    L = 0.f;
                     C.nscat[t] = (int)C.ev[t] - 1;
                     stage = ST_END_PACKET;
                     continue;
@@ -386,8 +432,8 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                 C.om[t] = om;
                 // forced scattering: tau_int from the exponential truncated at tau_path
                 const uint4 r = draw(C.ev[t], 0u);
-                const float tau_int = -log1pf(-u01f(r.x) * om_f);
-                C.tau_t[t] = (double)tau_int;
+                const float tau_int = -log1pf(-u01f(r.x) * om);
+                C.tau_t[t] = f2d(tau_int);
                 begin(M_LOCATE, k0, k1, k2);
                 rem_f = tau_int;
                 found = false;
@@ -398,28 +444,30 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
 
             if (stage == ST_LOCATE_DONE) {
                 C.c_loc[t] += nsteps;
-                double X0 = C.xd0[t], X1 = C.xd1[t], X2 = C.xd2[t];
-                const double K0 = k0, K1 = k1, K2 = k2;
+                float l0 = C.xl0[t], l1 = C.xl1[t], l2 = C.xl2[t];
                 if (found && last_axis >= 0) {
                     // entry point of the interaction cell, snapped onto the exact face plane
-                    const double te = (double)tcur;
-                    X0 += te * K0; X1 += te * K1; X2 += te * K2;
-                    if (last_axis == 0) X0 = Dlo0 + (double)(c0 + (s0 < 0)) * Dd0;
-                    else if (last_axis == 1) X1 = Dlo1 + (double)(c1 + (s1 < 0)) * Dd1;
-                    else X2 = Dlo2 + (double)(c2 + (s2 < 0)) * Dd2;
-                    const double si = (double)s_found;
-                    X0 += si * K0; X1 += si * K1; X2 += si * K2;
+                    df_add_prod(x0, l0, tcur, k0);
+                    df_add_prod(x1, l1, tcur, k1);
+                    df_add_prod(x2, l2, tcur, k2);
+                    if (last_axis == 0) { const float2 f = __ldg(fx + c0 + (s0 < 0)); x0 = f.x; l0 = f.y; }
+                    else if (last_axis == 1) { const float2 f = __ldg(fy + c1 + (s1 < 0)); x1 = f.x; l1 = f.y; }
+                    else { const float2 f = __ldg(fz + c2 + (s2 < 0)); x2 = f.x; l2 = f.y; }
+                    df_add_prod(x0, l0, s_found, k0);
+                    df_add_prod(x1, l1, s_found, k1);
+                    df_add_prod(x2, l2, s_found, k2);
                 } else {
-                    const double s = found ? (double)s_found : (double)last_dusty_end;
-                    X0 += s * K0; X1 += s * K1; X2 += s * K2;
+                    const float s = found ? s_found : last_dusty_end;
+                    df_add_prod(x0, l0, s, k0);
+                    df_add_prod(x1, l1, s, k1);
+                    df_add_prod(x2, l2, s, k2);
                 }
-                C.xd0[t] = X0; C.xd1[t] = X1; C.xd2[t] = X2;
-                x0 = (float)X0; x1 = (float)X1; x2 = (float)X2;
+                C.xl0[t] = l0; C.xl1[t] = l1; C.xl2[t] = l2;
                 have_pc = found;
                 if (found) { pc0 = c0; pc1 = c1; pc2 = c2; }
-                L = L * (double)C.alb[t] * C.om[t];
+                L = L * C.alb[t] * C.om[t];
                 C.nscat[t] = (int)C.ev[t];
-                if (L > 0.0 && A.peel && A.ninstr > 0) {
+                if (L > 0.f && A.peel && A.ninstr > 0) {
                     C.peel_kind[t] = 1;
                     C.peel_i[t] = 0;
                     C.after_peel[t] = ST_AFTER_SCATTER;
@@ -435,20 +483,24 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                 C.c_peel[t] += nsteps;
                 const int pi = C.peel_i[t];
                 const InstrDev& I = sins[pi];
-                const double w = C.peel_w[t];
-                if (w > 0.0) {
-                    const double flux = w * (double)expf(-(float)tau_hi) * I.flux_norm;
+                const float w = C.peel_w[t];
+                if (w > 0.f) {
+                    const float tobs = tau_hi_f + tau_lo;
+                    const float flux = w * expf(-tobs) * I.flux_norm_f;
                     C.p_peel[t] += flux;
-                    const double X0 = C.xd0[t], X1 = C.xd1[t], X2 = C.xd2[t];
-                    const double a = X0 * I.e1[0] + X1 * I.e1[1] + X2 * I.e1[2];
-                    const double b = X0 * I.e2[0] + X1 * I.e2[1] + X2 * I.e2[2];
-                    const double fa = floor((a + I.half_fov) * I.inv_dpx);
-                    const double fb = floor((b + I.half_fov) * I.inv_dpx);
-                    if (fa >= 0.0 && fa < (double)I.npx && fb >= 0.0 && fb < (double)I.npx) {
-                        const long long pix = (long long)fb * I.npx + (long long)fa;
-                        red_agg(A.images + I.img_off + pix * NL + lam, flux, wbuf);
-                    } else {
-                        red_agg(A.oof + (size_t)pi * NL + lam, flux, wbuf);
+                    const float a = x0 * I.e1_f[0] + x1 * I.e1_f[1] + x2 * I.e1_f[2] +
+                                    (C.xl0[t] * I.e1_f[0] + C.xl1[t] * I.e1_f[1] + C.xl2[t] * I.e1_f[2]);
+                    const float b = x0 * I.e2_f[0] + x1 * I.e2_f[1] + x2 * I.e2_f[2] +
+                                    (C.xl0[t] * I.e2_f[0] + C.xl1[t] * I.e2_f[1] + C.xl2[t] * I.e2_f[2]);
+                    const float fa = floorf((a + I.half_fov_f) * I.inv_dpx_f);
+                    const float fb = floorf((b + I.half_fov_f) * I.inv_dpx_f);
+                    if (flux >= 1.17549435e-38f) {
+                        if (fa >= 0.f && fa < (float)I.npx && fb >= 0.f && fb < (float)I.npx) {
+                            const long long pix = (long long)fb * I.npx + (long long)fa;
+                            red_agg(A.images + I.img_off + pix * NL + lam, f2d(flux), wbuf);
+                        } else {
+                            red_agg(A.oof + (size_t)pi * NL + lam, f2d(flux), wbuf);
+                        }
                     }
                 }
                 C.peel_i[t] = pi + 1;
@@ -458,7 +510,7 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
             }
 
             if (stage == ST_AFTER_SCATTER) {
-                if (L <= A.w_min * C.L0[t]) {
+                if (L <= A.w_min_f * C.L0[t]) {
                     C.p_res[t] += L;
                     stage = ST_END_PACKET;
                 } else if ((int)C.ev[t] >= A.max_events) {
@@ -479,22 +531,22 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
 
             // ST_END_PACKET
             C.c_scat[t] += (unsigned long long)C.nscat[t];
-            const double pe = C.p_esc[t], pa = C.p_abs[t], pr = C.p_res[t], pp = C.p_peel[t];
-            C.l_abs[t] += pa;
-            C.l_esc[t] += pe;
-            C.l_res[t] += pr;
+            const float pe = C.p_esc[t], pa = C.p_abs[t], pr = C.p_res[t], pp = C.p_peel[t];
+            C.l_abs[t] += f2d(pa);
+            C.l_esc[t] += f2d(pe);
+            C.l_res[t] += f2d(pr);
             if (!isfinite(pe + pa + pr + pp)) atomicOr(A.err, (unsigned)ERRBIT_NONFINITE);
             const unsigned pk = C.pk[t];
             if (pk < (unsigned)A.nrec) {
                 double* rec = A.records + ((size_t)lam * A.nrec + pk) * SKIRT_REC_FIELDS;
                 rec[0] = (double)C.nscat[t];
-                rec[1] = pe;
-                rec[2] = pa;
-                rec[3] = pr;
-                rec[4] = pp;
-                rec[5] = C.xd0[t];
-                rec[6] = C.xd1[t];
-                rec[7] = C.xd2[t];
+                rec[1] = f2d(pe);
+                rec[2] = f2d(pa);
+                rec[3] = f2d(pr);
+                rec[4] = f2d(pp);
+                rec[5] = f2d(x0) + f2d(C.xl0[t]);
+                rec[6] = f2d(x1) + f2d(C.xl1[t]);
+                rec[7] = f2d(x2) + f2d(C.xl2[t]);
             }
             stage = ST_NEW;
         }
@@ -507,8 +559,13 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
         if (!(sm | wm)) break;
         if (sm && (__popc(sm) >= step_min || !wm)) {
 #pragma unroll 1
-            for (int r = 0; r < ROUND; ++r)
+            for (int r = 0; r < ROUND; ++r) {
                 if (mode != M_NONE) step();
+                if (++wround == FLUSH) {
+                    wround = 0;
+                    flush();
+                }
+            }
             continue;
         }
         if (!stepping && alive) events();
