@@ -16,12 +16,13 @@
 //    peel-off line of sight).  A lane whose traversal ended idles until fewer
 //    than step_min lanes are still stepping; then the idle lanes handle
 //    their events (launch, scattering, peel-off tally) together.
-//  * Per cell crossing only FP32 arithmetic.  Optical depths of crossings are
-//    summed in FP32 and, every FLUSH warp rounds, the partial sums of all
-//    lanes are added to their FP64 running totals at once (one FP64
-//    instruction per warp).  The forced-interaction search compares in FP32
-//    against the remainder tau_int - (FP64 total).  Deposits are formed in
-//    FP32 and widened to FP64 by integer bit operations for the reduction.
+//  * Per cell crossing only FP32 arithmetic.  The optical depth of every
+//    crossing is FP32 and the running optical depth is their error-free
+//    double-float sum (Knuth two-sum: hi + lo, ~46-bit significand, exact
+//    up to its final rounding); at every event it is formed as an FP64
+//    value.  The sum depends only on the packet, never on the schedule.
+//    Deposits are formed in FP32 and widened to FP64 by integer bit
+//    operations for the reduction.
 //  * Positions are double-float pairs (hi + lo, ~48 bits).  Face planes come
 //    from exact per-grid tables; the distance from a start point to its first
 //    faces and the snapping of an interaction point onto the plane through
@@ -42,13 +43,10 @@ namespace skirt {
 namespace {
 
 constexpr int MAXB = 256;  // threads per block of the mixed kernel (upper bound)
-constexpr int FLUSH = 32;  // warp rounds between FP64 accumulations of the optical depth
 constexpr int ROUND = 4;   // cell crossings per stepping round between warp votes
 
-// FP32 -> FP64 and FP64 -> FP32 by IEEE-754 field manipulation on the
-// integer pipe.  f2d is exact for normal floats (zero and FP32 subnormals map
-// to zero); d2f truncates towards zero (FP64 values outside the FP32 range
-// saturate to zero / infinity).
+// FP32 -> FP64 by IEEE-754 field manipulation on the integer pipe: exact for
+// normal floats; zero and FP32 subnormals map to zero.
 __device__ __forceinline__ double f2d(float f)
 {
     const unsigned u = __float_as_uint(f);
@@ -59,14 +57,15 @@ __device__ __forceinline__ double f2d(float f)
     return ex ? __longlong_as_double((long long)bits) : 0.0;
 }
 
-__device__ __forceinline__ float d2f(double d)
+// (hi, lo) += v, error-free: hi takes the rounded sum, lo collects the exact
+// rounding errors (two-sum).
+__device__ __forceinline__ void df_accumulate(float& hi, float& lo, float v)
 {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
-    const int ex = (int)((u >> 52) & 0x7FF) - 896;
-    const unsigned sign = (unsigned)(u >> 63) << 31;
-    if (ex <= 0) return __uint_as_float(sign);
-    if (ex >= 255) return __uint_as_float(sign | 0x7F800000u);
-    return __uint_as_float(sign | ((unsigned)ex << 23) | (unsigned)((u >> 29) & 0x7FFFFFu));
+    const float s = __fadd_rn(hi, v);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
 }
 
 // Double-float arithmetic (Knuth / Dekker error-free transformations), with
@@ -89,7 +88,6 @@ __device__ __forceinline__ float df_diff(float2 f, float xh, float xl)
 
 // Per-thread state used only at events, struct of arrays in shared memory.
 struct Cold {
-    double tau_t[MAXB];
     double l_emit[MAXB], l_abs[MAXB], l_esc[MAXB], l_res[MAXB];
     unsigned long long q[MAXB], q_end[MAXB];
     unsigned long long c_dep[MAXB], c_loc[MAXB], c_peel[MAXB], c_scat[MAXB];
@@ -134,14 +132,13 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
     int mode = M_NONE;
     int c0 = 0, c1 = 0, c2 = 0, s0 = 0, s1 = 0, s2 = 0;
     float iv0 = 0.f, iv1 = 0.f, iv2 = 0.f, tn0 = 0.f, tn1 = 0.f, tn2 = 0.f, tcur = 0.f;
-    double tau_hi = 0.0;
-    float tau_lo = 0.f, tau_hi_f = 0.f, rem_f = 0.f;
+    float tau_h = 0.f, tau_l = 0.f;  // running optical depth of the traversal (double-float)
+    float rem_f = 0.f;               // interaction optical depth (search)
     unsigned nsteps = 0;
     float labs_f = 0.f;
     float s_found = 0.f, last_dusty_end = 0.f;
     bool found = false;
-    int last_axis = -1;   // axis of the face through which the current cell was entered
-    unsigned wround = 0;  // warp-uniform round counter
+    int last_axis = -1;  // axis of the face through which the current cell was entered
     // ---- packet state (registers)
     int stage = ST_NEW;
     bool alive = true;
@@ -180,8 +177,7 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
         tn1 = s1 ? df_diff(__ldg(fy + c1 + (s1 > 0)), x1, l1) * iv1 : INF;
         tn2 = s2 ? df_diff(__ldg(fz + c2 + (s2 > 0)), x2, l2) * iv2 : INF;
         tcur = 0.f;
-        tau_hi = 0.0;
-        tau_lo = tau_hi_f = 0.f;
+        tau_h = tau_l = 0.f;
         nsteps = 0;
         last_axis = -1;
     };
@@ -196,10 +192,11 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
         const float dtau = krl * ds;
         ++nsteps;
         bool done = false;
+        const float tau_prev = tau_h + tau_l;
         if (mode == M_LOCATE) {
             if (krl > 0.f) {
-                if (tau_lo + dtau >= rem_f) {
-                    s_found = (rem_f - tau_lo) / krl;  // distance inside the current cell
+                if (tau_h + (tau_l + dtau) >= rem_f) {
+                    s_found = (rem_f - tau_prev) / krl;  // distance inside the current cell
                     found = true;
                     done = true;
                 } else {
@@ -207,10 +204,10 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                 }
             }
         } else if (mode == M_DEPOSIT && dtau > 0.f) {
-            const float dep = labs_f * expf(-(tau_hi_f + tau_lo)) * (-expm1f(-dtau));
+            const float dep = labs_f * expf(-tau_prev) * (-expm1f(-dtau));
             if (dep >= 1.17549435e-38f) atomicAdd(absorbed + (size_t)m * NL + lam, f2d(dep));
         }
-        tau_lo += dtau;
+        df_accumulate(tau_h, tau_l, dtau);
         if (!done) {
             tcur = tmin;
             const int cs = axis == 0 ? c0 : (axis == 1 ? c1 : c2);
@@ -232,16 +229,6 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
             }
         }
         if (done) mode = M_NONE;
-    };
-
-    // FP64 accumulation of the lanes' partial optical depths (warp-uniform call)
-    auto flush = [&]() {
-        if (mode != M_NONE) {
-            tau_hi += f2d(tau_lo);
-            tau_lo = 0.f;
-            tau_hi_f = d2f(tau_hi);
-            if (mode == M_LOCATE) rem_f = d2f(C.tau_t[t] - tau_hi);
-        }
     };
 
     auto draw = [&](uint32_t event, uint32_t block) -> uint4 {
@@ -413,10 +400,10 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
 
             if (stage == ST_DEPOSIT_DONE) {
                 C.c_dep[t] += nsteps;
-                const double tau_path = tau_hi + f2d(tau_lo);
+                const double tau_path = f2d(tau_h) + f2d(tau_l);  // the path's optical depth, FP64
                 // om = 1 - e^{-tau_path}: from expm1 for small tau, from 1 - exp for
                 // large tau, so that both om and 1 - om keep FP32 relative precision
-                const float tf = d2f(tau_path);
+                const float tf = tau_h + tau_l;
                 float om, E;
                 if (tf < 0.6931472f) { om = -expm1f(-tf); E = 1.f - om; }
                 else { E = expf(-tf); om = 1.f - E; }
@@ -433,7 +420,6 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                 // forced scattering: tau_int from the exponential truncated at tau_path
                 const uint4 r = draw(C.ev[t], 0u);
                 const float tau_int = -log1pf(-u01f(r.x) * om);
-                C.tau_t[t] = f2d(tau_int);
                 begin(M_LOCATE, k0, k1, k2);
                 rem_f = tau_int;
                 found = false;
@@ -485,7 +471,7 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                 const InstrDev& I = sins[pi];
                 const float w = C.peel_w[t];
                 if (w > 0.f) {
-                    const float tobs = tau_hi_f + tau_lo;
+                    const float tobs = tau_h + tau_l;
                     const float flux = w * expf(-tobs) * I.flux_norm_f;
                     C.p_peel[t] += flux;
                     const float a = x0 * I.e1_f[0] + x1 * I.e1_f[1] + x2 * I.e1_f[2] +
@@ -559,13 +545,8 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
         if (!(sm | wm)) break;
         if (sm && (__popc(sm) >= step_min || !wm)) {
 #pragma unroll 1
-            for (int r = 0; r < ROUND; ++r) {
+            for (int r = 0; r < ROUND; ++r)
                 if (mode != M_NONE) step();
-                if (++wround == FLUSH) {
-                    wround = 0;
-                    flush();
-                }
-            }
             continue;
         }
         if (!stepping && alive) events();

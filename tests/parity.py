@@ -1,25 +1,39 @@
 """Comparison helpers for GPU-vs-oracle parity (shared by the GPU tests).
 
-Tolerances (derivations in the design notes):
+Tolerances:
 * FP64 form: the GPU replays the oracle's packet histories with the same
   Philox streams; the only differences are rounding order (atomic
   accumulation order, exp/log implementations, reciprocal instead of
-  division).  Per-packet records and tallies agree to 1e-9 relative.
-* Mixed form: FP32 positions, directions and per-cell optical depths.
-  Per-packet continuous quantities within 1e-5 relative; at least 99.9% of
-  packets take the same number of scatterings (a packet whose luminosity
-  lands within FP32 rounding of the w_min threshold may fork); tallies within
-  1e-4 relative for cells / pixels holding at least 1e-6 of the total and an
-  L1-normalised difference below 1e-4.  Pixel indices are decided by FP32
-  positions, so a peel-off within ~|x| 2^-22 of a pixel border can land in
-  the neighbouring pixel: images are compared through their L1-normalised
-  difference with the bound img_l1_bound().
+  division).  Per-packet records (fields scaled by the packet's launch
+  luminosity, positions by the grid extent) and tallies agree to 1e-9.
+* Mixed form, smooth media: FP32 traversal with ~2^-24 relative error per
+  crossing.  At least 99.9% of the packets take the same number of
+  scatterings with every record field within 1e-5 of its scale; tallies:
+  L1-normalised difference below 1e-4 and every cell holding at least 1e-4
+  of the total within 1e-4 (a cell's error averages its contributions; a
+  sparsely hit cell can be dominated by one short corner segment whose FP32
+  length carries an absolute error ~|x| 2^-24).  Pixel indices are decided
+  by FP32 positions, so a peel-off within ~|x| 2^-22 of a pixel border can
+  land in the neighbouring pixel: images are compared through their
+  L1-normalised difference with the bound img_l1_bound().
+* Clumpy media (100x density contrast): packet histories are chaotic -- a
+  path that grazes a clump boundary moves the next interaction point by up
+  to the contrast times the perturbation.  The FP64 form already departs
+  from the oracle by up to ~1e-8 there (rounding-level differences
+  amplified).  For the mixed form: at least 99.9% of packets take the same
+  number of scatterings and at least 90% match every field within 1e-5;
+  aggregated tallies keep the L1-normalised bound 1e-4; well-sampled cells
+  (>= 1e-4 of the total) within CHAOTIC_CELL and the SEDs within
+  CHAOTIC_SED.
 """
 import numpy as np
 
 REL_FP64 = 1e-9
 REL_MIXED_PACKET = 1e-5
 REL_MIXED_TALLY = 1e-4
+MIXED_CELL_SIGNIFICANT = 1e-4
+CHAOTIC_CELL = 5e-3
+CHAOTIC_SED = 1e-3
 
 
 def rel_err(a, b, floor):
@@ -39,11 +53,12 @@ def record_scales(prob):
     return L0, norm, extent
 
 
-def compare_records(gpu, ref, prob, rel, min_match=1.0):
+def compare_records(gpu, ref, prob, rel, min_match=1.0, same_n_min=None):
     """gpu, ref: [nlambda, nrec, 8] records of the same packets.  A packet
     matches when it took the same number of scatterings and every other field
     agrees within rel of its scale (record_scales).  Returns the matching
-    fraction over packets that exist; asserts it is >= min_match."""
+    fraction over packets that exist; asserts it is >= min_match, and that
+    the fraction with the same number of scatterings is >= same_n_min."""
     gpu = np.asarray(gpu, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
     assert gpu.shape == ref.shape
@@ -58,6 +73,9 @@ def compare_records(gpu, ref, prob, rel, min_match=1.0):
     ok = (gpu[..., 0] == ref[..., 0]) & np.all(err <= rel, axis=-1)
     ok = ok[exists]
     frac = ok.mean() if ok.size else 1.0
+    if same_n_min is not None and ok.size:
+        same = (gpu[..., 0] == ref[..., 0])[exists].mean()
+        assert same >= same_n_min, ("scattering counts", same)
     bad = np.argwhere(exists & ~((gpu[..., 0] == ref[..., 0]) & np.all(err <= rel, axis=-1)))
     assert frac >= min_match, (frac, bad[:10], gpu[tuple(bad[:3].T)], ref[tuple(bad[:3].T)])
     return frac

@@ -7,8 +7,8 @@ import pytest
 
 from paper_1705_04702_gb300 import workloads as W
 
-from parity import (REL_FP64, REL_MIXED_PACKET, REL_MIXED_TALLY, compare_records, compare_tally,
-                    img_l1_bound)
+from parity import (CHAOTIC_CELL, CHAOTIC_SED, MIXED_CELL_SIGNIFICANT, REL_FP64, REL_MIXED_PACKET,
+                    REL_MIXED_TALLY, compare_records, compare_tally, img_l1_bound)
 
 pytestmark = pytest.mark.gpu
 
@@ -33,21 +33,29 @@ def _extent(prob):
     return max(b[1] - b[0], b[3] - b[2], b[5] - b[4])
 
 
-def _check(S, oracle_lib, prob, precision, nrec=0, **kw):
+def _check(S, oracle_lib, prob, precision, nrec=0, chaotic=False, **kw):
     nrec = nrec or int(min(prob.npk.max(), 4000))
     g = S.run_problem(prob, precision=precision, nrec=nrec, **kw)
     r = oracle_lib.trace(prob, nrec=nrec)
     fp64 = precision == S.PREC_FP64
     rel_p = REL_FP64 if fp64 else REL_MIXED_PACKET
     rel_t = REL_FP64 if fp64 else REL_MIXED_TALLY
-    compare_records(_np(g["records"]), r["records"], prob, rel_p, 0.999)
-    compare_tally(_np(g["absorbed"]), r["absorbed"], rel_t)
+    if fp64:
+        compare_records(_np(g["records"]), r["records"], prob, rel_p, 0.999, same_n_min=1.0)
+        compare_tally(_np(g["absorbed"]), r["absorbed"], rel_t)
+    elif not chaotic:
+        compare_records(_np(g["records"]), r["records"], prob, rel_p, 0.999, same_n_min=0.999)
+        compare_tally(_np(g["absorbed"]), r["absorbed"], rel_t, significant=MIXED_CELL_SIGNIFICANT)
+    else:
+        compare_records(_np(g["records"]), r["records"], prob, rel_p, 0.90, same_n_min=0.999)
+        compare_tally(_np(g["absorbed"]), r["absorbed"], CHAOTIC_CELL, significant=MIXED_CELL_SIGNIFICANT,
+                      l1=REL_MIXED_TALLY)
     if prob.instruments:
-        compare_tally(_np(g["sed"]), r["sed"], rel_t, significant=0.0)
+        compare_tally(_np(g["sed"]), r["sed"], CHAOTIC_SED if chaotic and not fp64 else rel_t, significant=0.0)
         compare_tally(_np(g["images_flat"]), r["images_flat"], rel_t if fp64 else 1.0,
                       significant=1e-6 if fp64 else 1.1, l1=rel_t if fp64 else img_l1_bound(prob))
     led = g["ledger_per_lambda"]
-    np.testing.assert_allclose(led, r["ledger"], rtol=rel_t, atol=1e-300)
+    np.testing.assert_allclose(led, r["ledger"], rtol=CHAOTIC_SED if chaotic and not fp64 else rel_t, atol=1e-300)
     tot = g["ledger"]
     closure = abs(tot["emitted"] - tot["absorbed"] - tot["escaped"] - tot["residual"]) / max(tot["emitted"], 1e-300)
     assert closure < (1e-12 if fp64 else 1e-6), closure
@@ -76,7 +84,7 @@ def test_disk_multi_wavelength(S, oracle_lib, precision):
 def test_torus_uneven_counts(S, oracle_lib, precision):
     prob = W.torus_problem(n=48, nlambda=12, packet_scale=2e-4, npx=48)
     prob.npk[3] = 0  # an empty wavelength in the middle
-    _check(S, oracle_lib, prob, precision)
+    _check(S, oracle_lib, prob, precision, chaotic=True)
 
 
 @pytest.mark.parametrize("schedule", [0, 1], ids=["per_lambda", "persistent"])
@@ -124,7 +132,8 @@ def test_edge_cases(S, oracle_lib):
                      W.single_wavelength(), np.array([1000], np.uint64), [W.Instrument(10.0, 0.0, 0.0, 2.0, 8)])
     g = S.run_problem(prob, nrec=10)
     assert float(g["absorbed"].abs().sum()) == 0
-    assert g["ledger"]["escaped"] == pytest.approx(1.0, rel=1e-12)
+    # mixed form: the packet luminosity 1/1000 is an FP32 value
+    assert g["ledger"]["escaped"] == pytest.approx(1.0, rel=1e-7)
     assert float(g["sed"][0, 0]) == pytest.approx(1.0 / (4 * math.pi * 100), rel=1e-6)
     # no instruments, and peel-off disabled
     prob = W.sphere_problem(2000)
