@@ -222,9 +222,10 @@ def main():
     opts.use_graph = 1
     tune = None
     if args.autotune:
-        S.skirt_autotune(grid.h, src, tables.c, prob.npk, seed, ins, opts, 0.01, absorbed, images, sed,
+        S.skirt_autotune(grid.h, src, tables.c, prob.npk, seed, ins, opts, 0.02, absorbed, images, sed,
                          stream=stream.cuda_stream)
-        tune = {"block": opts.block, "chunk": opts.chunk, "blocks_per_sm": opts.blocks_per_sm}
+        tune = {"block": opts.block, "chunk": opts.chunk, "blocks_per_sm": opts.blocks_per_sm,
+                "step_min": opts.step_min, "autotuned": True}
 
     def step():
         return S.skirt_trace(grid.h, src, tables.c, prob.npk, seed, ins, opts, absorbed, images, sed,

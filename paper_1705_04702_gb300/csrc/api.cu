@@ -618,37 +618,44 @@ extern "C" int skirt_autotune(skirt_grid_t g, const skirt_source* src, const ski
     o.accumulate = 0;
     o.nrec = 0;
     o.records = nullptr;
-    const int blocks[4] = {64, 128, 256, o.precision == SKIRT_PREC_MIXED ? 256 : 512};
-    const int chunks[5] = {1, 2, 4, 8, 16};
+    const bool mixed = o.precision == SKIRT_PREC_MIXED;
+    const int blocks[4] = {64, 128, 256, mixed ? 256 : 512};
+    const int chunks[3] = {1, 4, 16};
+    const int step_mins[3] = {8, 16, 24};
     float best = 1e30f;
-    int bb = 256, bc = 4, bbps = 0;
+    int bb = 256, bc = 4, bbps = 0, bsm = 16;
     for (int bi = 0; bi < 4; ++bi) {
         if (bi > 0 && blocks[bi] == blocks[bi - 1]) continue;
         int maxbps = 0;
         CK(trace_occupancy(o.precision, blocks[bi], &maxbps));
         if (maxbps < 1) continue;
-        for (int ci = 0; ci < 5; ++ci) {
-            for (int bps = maxbps; bps >= 1; bps = (bps > 1 ? (bps + 1) / 2 : 0)) {
-                o.block = blocks[bi];
-                o.chunk = chunks[ci];
-                o.blocks_per_sm = bps;
-                skirt_ledger led;
-                int r = skirt_trace(g, src, wl, sample.data(), seed, ins, ninstr, &o, absorbed, images, sed, &led,
-                                    nullptr, stream);
-                if (r && r != SKIRT_ERR_EVENT_CAP) return r;
-                if (led.kernel_ms > 0 && led.kernel_ms < best) {
-                    best = led.kernel_ms;
-                    bb = blocks[bi];
-                    bc = chunks[ci];
-                    bbps = bps;
+        for (int ci = 0; ci < 3; ++ci) {
+            for (int si = 0; si < (mixed ? 3 : 1); ++si) {
+                for (int bps = maxbps; bps >= 1; bps = (bps > 1 ? (bps + 1) / 2 : 0)) {
+                    o.block = blocks[bi];
+                    o.chunk = chunks[ci];
+                    o.step_min = step_mins[si];
+                    o.blocks_per_sm = bps;
+                    skirt_ledger led;
+                    int r = skirt_trace(g, src, wl, sample.data(), seed, ins, ninstr, &o, absorbed, images, sed,
+                                        &led, nullptr, stream);
+                    if (r && r != SKIRT_ERR_EVENT_CAP) return r;
+                    if (led.kernel_ms > 0 && led.kernel_ms < best) {
+                        best = led.kernel_ms;
+                        bb = blocks[bi];
+                        bc = chunks[ci];
+                        bbps = bps;
+                        bsm = step_mins[si];
+                    }
+                    if (bps == 1) break;
                 }
-                if (bps == 1) break;
             }
         }
     }
     opts->block = bb;
     opts->chunk = bc;
     opts->blocks_per_sm = bbps;
+    opts->step_min = bsm;
     // leave the outputs zeroed
     skirt_trace_opts z = o;
     std::vector<uint64_t> none(wl->n, 0);
