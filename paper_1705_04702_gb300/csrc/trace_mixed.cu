@@ -57,6 +57,22 @@ __device__ __forceinline__ double f2d(float f)
     return ex ? __longlong_as_double((long long)bits) : 0.0;
 }
 
+// e^{-x} for x >= 0 as 2^{-x log2 e}; its error is that of the FP32 product
+// x log2 e, i.e. of the same order as the FP32 rounding of x itself.
+__device__ __forceinline__ float exp_neg(float x) { return exp2f(-1.4426950408889634f * x); }
+
+// 1 - e^{-x} for x >= 0, accurate in relative terms: the alternating Taylor
+// series x - x^2/2! + ... + x^7/7! (Horner form) below 1/4, where the first
+// omitted term is below 4e-10 of the result; 1 - e^{-x} above, where no
+// cancellation occurs.  Both branches are evaluated and selected.
+__device__ __forceinline__ float one_minus_exp_neg(float x)
+{
+    const float p = x * (1.f - x * (1.f / 2.f) * (1.f - x * (1.f / 3.f) * (1.f - x * (1.f / 4.f) *
+                        (1.f - x * (1.f / 5.f) * (1.f - x * (1.f / 6.f) * (1.f - x * (1.f / 7.f)))))));
+    const float q = 1.f - exp_neg(x);
+    return x < 0.25f ? p : q;
+}
+
 // (hi, lo) += v, error-free: hi takes the rounded sum, lo collects the exact
 // rounding errors (two-sum).
 __device__ __forceinline__ void df_accumulate(float& hi, float& lo, float v)
@@ -139,6 +155,9 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
     float s_found = 0.f, last_dusty_end = 0.f;
     bool found = false;
     int last_axis = -1;  // axis of the face through which the current cell was entered
+    int cur_m = 0;       // index of the current cell
+    float kr_cur = 0.f;  // its extinction coefficient (loaded one crossing ahead)
+    const int nxy = nx * ny;
     // ---- packet state (registers)
     int stage = ST_NEW;
     bool alive = true;
@@ -180,15 +199,26 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
         tau_h = tau_l = 0.f;
         nsteps = 0;
         last_axis = -1;
+        cur_m = (c2 * ny + c1) * nx + c0;
+        kr_cur = __ldg(kr + cur_m);
     };
 
     // one cell crossing of the current traversal
     auto step = [&]() {
         const float tmin = fminf(fminf(tn0, tn1), tn2);
         const int axis = (tn0 == tmin) ? 0 : ((tn1 == tmin) ? 1 : 2);
+        // the next cell is known before the current one is processed: issue
+        // its density load now so that it overlaps with this crossing's work
+        const int cs = axis == 0 ? c0 : (axis == 1 ? c1 : c2);
+        const int ss = axis == 0 ? s0 : (axis == 1 ? s1 : s2);
+        const int na = axis == 0 ? nx : (axis == 1 ? ny : nz);
+        const int cn = cs + ss;
+        const bool out = (unsigned)cn >= (unsigned)na;
+        const int mn = cur_m + ss * (axis == 0 ? 1 : (axis == 1 ? nx : nxy));
+        const float kr_next = out ? 0.f : __ldg(kr + mn);
         const float ds = fmaxf(tmin - tcur, 0.f);
-        const int m = (c2 * ny + c1) * nx + c0;
-        const float krl = __ldg(kr + m) * krs;
+        const int m = cur_m;
+        const float krl = kr_cur * krs;
         const float dtau = krl * ds;
         ++nsteps;
         bool done = false;
@@ -204,19 +234,17 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                 }
             }
         } else if (mode == M_DEPOSIT && dtau > 0.f) {
-            const float dep = labs_f * expf(-tau_prev) * (-expm1f(-dtau));
+            const float dep = labs_f * exp_neg(tau_prev) * one_minus_exp_neg(dtau);
             if (dep >= 1.17549435e-38f) atomicAdd(absorbed + (size_t)m * NL + lam, f2d(dep));
         }
         df_accumulate(tau_h, tau_l, dtau);
         if (!done) {
             tcur = tmin;
-            const int cs = axis == 0 ? c0 : (axis == 1 ? c1 : c2);
-            const int ss = axis == 0 ? s0 : (axis == 1 ? s1 : s2);
-            const int na = axis == 0 ? nx : (axis == 1 ? ny : nz);
-            const int cn = cs + ss;
-            if ((unsigned)cn >= (unsigned)na) {
+            if (out) {
                 done = true;
             } else {
+                cur_m = mn;
+                kr_cur = kr_next;
                 const float loa = axis == 0 ? lo0 : (axis == 1 ? lo1 : lo2);
                 const float da = axis == 0 ? d0 : (axis == 1 ? d1 : d2);
                 const float xa = axis == 0 ? x0 : (axis == 1 ? x1 : x2);
