@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--workload", default="disk", choices=["disk", "disk40", "torus"],
+                    help="disk: 1 wavelength, --packets packets (default); disk40: 40 wavelengths, "
+                         "--packets per wavelength; torus: clumpy torus, 200 wavelengths, uneven counts "
+                         "(--packets scales them, 1e8 = the full 7.5e8-packet run)")
     return ap.parse_args()
 
 
@@ -61,13 +65,28 @@ def peaks():
 
 def workload(args):
     from paper_1705_04702_gb300 import workloads as W
+    if args.workload == "disk40":
+        return W.disk_problem(int(args.packets), n=args.grid, nlambda=40, npx=512)
+    if args.workload == "torus":
+        return W.torus_problem(n=args.grid, nlambda=200, npx=512, packet_scale=args.packets / 1e8)
     return W.disk_problem(int(args.packets), n=args.grid, nlambda=1, npx=512)
+
+
+def workload_name(args, prob):
+    if args.workload == "disk40":
+        return (f"exponential-disk galaxy, {args.grid}^3 Cartesian grid, 40 wavelengths 0.1-5 um, "
+                f"{int(args.packets):.0e} packets per wavelength, 3 instruments 512x512 (i=0/60/90)")
+    if args.workload == "torus":
+        return (f"clumpy two-phase dust torus, {args.grid}^3 Cartesian grid, 200 wavelengths 0.09-10 um, "
+                f"{prob.total_packets:.3e} packets (1e5-2e7 per wavelength, log-uniform), "
+                f"3 instruments 512x512 (i=0/60/90)")
+    return (f"exponential-disk galaxy, {args.grid}^3 Cartesian grid, 1 wavelength (0.55 um), "
+            f"{int(args.packets):.0e} packets, 3 instruments 512x512 (i=0/60/90)")
 
 
 def config_of(args, prob, extra=None):
     c = {
-        "workload": f"exponential-disk galaxy, {args.grid}^3 Cartesian grid, 1 wavelength (0.55 um), "
-                    f"{int(args.packets):.0e} packets, 3 instruments 512x512 (i=0/60/90)",
+        "workload": workload_name(args, prob),
         "grid": args.grid,
         "nlambda": prob.wl.n,
         "packets_per_step": prob.total_packets,
@@ -179,12 +198,13 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        n = args.cpu_packets
+        per = max(1, args.cpu_packets // prob.wl.n)  # packets per wavelength in the sample
+        n = int(np.minimum(prob.npk, per).sum())
         t0 = time.perf_counter()
-        oracle.trace(prob, 0, n)
+        oracle.trace(prob, 0, per)
         dt = time.perf_counter() - t0
         cpu = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"packets 0..{n - 1} of the {int(args.packets):.0e}-packet workload, "
+               "sample": f"packets 0..{per - 1} of every wavelength ({n} packet-wavelengths) of the workload, "
                          f"single-threaded FP64, {dt:.1f} s"}
 
     import torch
@@ -277,7 +297,8 @@ def main():
     # ---- plain FP64 form, one launch per wavelength, on a sample
     fp64 = None
     if args.fp64_packets > 0:
-        p64 = prob.with_packets(int(args.fp64_packets))
+        frac64 = min(1.0, args.fp64_packets / max(prob.total_packets, 1))
+        p64 = prob.with_packets(np.round(prob.npk.astype(np.float64) * frac64).astype(np.uint64))
         o64 = S.skirt_trace_opts_default()
         o64.precision = S.PREC_FP64
         o64.schedule = S.SCHED_PER_LAMBDA

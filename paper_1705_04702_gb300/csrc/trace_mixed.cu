@@ -42,8 +42,9 @@
 namespace skirt {
 namespace {
 
-constexpr int MAXB = 256;  // threads per block of the mixed kernel (upper bound)
-constexpr int ROUND = 4;   // cell crossings per stepping round between warp votes
+constexpr int MAXB = 256;       // threads per block of the mixed kernel (upper bound)
+constexpr int ROUND = 4;        // cell crossings per stepping round between warp votes
+constexpr float TAU_CUT = 50.f; // optical depth after which a deposit / peel-off traversal stops
 
 // FP32 -> FP64 by IEEE-754 field manipulation on the integer pipe: exact for
 // normal floats; zero and FP32 subnormals map to zero.
@@ -57,9 +58,16 @@ __device__ __forceinline__ double f2d(float f)
     return ex ? __longlong_as_double((long long)bits) : 0.0;
 }
 
-// e^{-x} for x >= 0 as 2^{-x log2 e}; its error is that of the FP32 product
-// x log2 e, i.e. of the same order as the FP32 rounding of x itself.
-__device__ __forceinline__ float exp_neg(float x) { return exp2f(-1.4426950408889634f * x); }
+// e^{-x} for x >= 0 as 2^{-x log2 e} with the PTX base-2 exponential
+// (ex2.approx, relative error ~2^-22); the FP32 product x log2 e contributes
+// an error of the same order as the FP32 rounding of x itself.  Results below
+// the FP32 normal range flush to zero.
+__device__ __forceinline__ float exp_neg(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-1.4426950408889634f * x));
+    return y;
+}
 
 // 1 - e^{-x} for x >= 0, accurate in relative terms: the alternating Taylor
 // series x - x^2/2! + ... + x^7/7! (Horner form) below 1/4, where the first
@@ -250,12 +258,20 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                 const float xa = axis == 0 ? x0 : (axis == 1 ? x1 : x2);
                 const float iva = axis == 0 ? iv0 : (axis == 1 ? iv1 : iv2);
                 const float tnew = (loa + (float)(cn + (ss > 0)) * da - xa) * iva;
-                if (axis == 0) { c0 = cn; tn0 = tnew; }
-                else if (axis == 1) { c1 = cn; tn1 = tnew; }
-                else { c2 = cn; tn2 = tnew; }
+                c0 = axis == 0 ? cn : c0;
+                c1 = axis == 1 ? cn : c1;
+                c2 = axis == 2 ? cn : c2;
+                tn0 = axis == 0 ? tnew : tn0;
+                tn1 = axis == 1 ? tnew : tn1;
+                tn2 = axis == 2 ? tnew : tn2;
                 last_axis = axis;
             }
         }
+        // Beyond tau = TAU_CUT a line of sight transmits < e^-50 and a deposit
+        // path has handed < e^-50 of the luminosity to its remaining cells:
+        // the traversal ends there (the search never gets that far, since
+        // tau_int < 17 in FP32).
+        if (tau_h > TAU_CUT && mode != M_LOCATE) done = true;
         if (done) mode = M_NONE;
     };
 
