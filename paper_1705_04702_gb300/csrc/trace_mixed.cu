@@ -58,6 +58,15 @@ __device__ __forceinline__ double f2d(float f)
     return ex ? __longlong_as_double((long long)bits) : 0.0;
 }
 
+// FP32 -> FP64 for a positive normal float: the double's high word is the
+// float's bits shifted right by 3 with the exponent re-biased by 1023 - 127,
+// its low word the three mantissa bits shifted out.
+__device__ __forceinline__ double f2d_pos(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    return __hiloint2double((int)((u >> 3) + 0x38000000u), (int)(u << 29));
+}
+
 // e^{-x} for x >= 0 as 2^{-x log2 e} with the PTX base-2 exponential
 // (ex2.approx, relative error ~2^-22); the FP32 product x log2 e contributes
 // an error of the same order as the FP32 rounding of x itself.  Results below
@@ -243,7 +252,7 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
             }
         } else if (mode == M_DEPOSIT && dtau > 0.f) {
             const float dep = labs_f * exp_neg(tau_prev) * one_minus_exp_neg(dtau);
-            if (dep >= 1.17549435e-38f) atomicAdd(absorbed + (size_t)m * NL + lam, f2d(dep));
+            if (dep >= 1.17549435e-38f) atomicAdd(absorbed + (size_t)m * NL + lam, f2d_pos(dep));
         }
         df_accumulate(tau_h, tau_l, dtau);
         if (!done) {

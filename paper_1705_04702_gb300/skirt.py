@@ -223,7 +223,7 @@ class Grid:
 
 
 def run_problem(prob, grid: Grid | None = None, precision=PREC_MIXED, schedule=SCHED_PERSISTENT, nrec=0,
-                use_graph=False, peel=True, block=0, chunk=0, blocks_per_sm=0, outputs=None, emission=None,
+                use_graph=False, peel=True, block=0, chunk=0, blocks_per_sm=0, step_min=0, outputs=None, emission=None,
                 device="cuda", stream=None, accumulate=False):
     """Traces a workloads.Problem on the GPU; returns a dict of torch tensors
     (absorbed [ncell, n], images list [npx, npx, n], sed [ninstr, n], records)
@@ -253,6 +253,7 @@ def run_problem(prob, grid: Grid | None = None, precision=PREC_MIXED, schedule=S
     o.block = block
     o.chunk = chunk
     o.blocks_per_sm = blocks_per_sm
+    o.step_min = step_min
     o.use_graph = 1 if use_graph else 0
     o.phase = prob.phase
     o.nrec = nrec
