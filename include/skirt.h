@@ -202,6 +202,104 @@ int skirt_autotune(skirt_grid_t grid, const skirt_source* src, const skirt_wavel
                    skirt_trace_opts* opts, double sample_fraction, double* absorbed,
                    double* images, double* sed, void* stream);
 
+/* ---------------------------------------------------------- dust emission */
+/* Dust emission phase (Sect. 3.2: the emission spectrum of every dust cell
+ * is computed from the amount of absorbed radiation; Sect. 1: instantaneous
+ * dust emission).  Model (the paper gives none; equilibrium emission of three
+ * grain populations):
+ *   absorption shares w_i(lambda) ~ (lambda/0.55um)^delta_i, delta = (-0.5, 0, 0.5),
+ *     normalised to sum 1; P_i(m) = sum_j w_i(lambda_j) absorbed(m, j);
+ *   output grid: 100 wavelengths log-spaced over 1-1000 um, trapezoid weights W_l;
+ *   opacities kappa_i = (lambda/100um)^-beta_i, beta = (1.5, 2, 2);
+ *   B(lambda, T) = lambda^-5 / (exp(hc/(k lambda T)) - 1);
+ *   energy balance M c_i G_i(T_i) = P_i, G_i(T) = sum_l W_l kappa_i B(lambda_l, T),
+ *     c_i = 1/G_i(30 K), M = dust mass of the cell (extinction coefficient x volume);
+ *     T_i by bracketed Newton on ln T in [3, 2000] K (FP64, clamped);
+ *   emission(m, l) = sum_i P_i W_l kappa_i B(lambda_l, T_i) / G_i(T_i)
+ *     (luminosity in output bin l; the row sums to the absorbed power). */
+enum { SKIRT_EMIT_EXACT = 0, SKIRT_EMIT_SURROGATE = 1 };
+enum { SKIRT_NBANDS = 32, SKIRT_NEMIT = 100, SKIRT_MLP_HIDDEN = 128 };
+/* Number of floats in a packed parameter vector: W1[128][32] b1[128]
+ * W2[128][128] b2[128] W3[100][128] b3[100] (rows = outputs). */
+enum { SKIRT_MLP_NPARAM = 128 * 32 + 128 + 128 * 128 + 128 + 100 * 128 + 100 };
+
+/* The output wavelength grid: lambda[100] in micron and its trapezoid
+ * weights W[100] (host arrays, either may be NULL). */
+int skirt_emission_grid(double* lambda_um, double* weights);
+
+/* Dust mass of every cell, M = kr * cell volume (device float[ncell]). */
+int skirt_dust_mass(skirt_grid_t grid, float* mass, void* stream);
+
+/* Band compression: B_b(m) = sum of absorbed(m, j) over the input
+ * wavelengths j in band b, 32 bands log-spaced over [min, max] of lambda_in;
+ * features(m, b) = log10(max(B_b / M, 1e-30)) (0 .. -30 for dust-free cells),
+ * total(m) = sum_j absorbed(m, j).  absorbed: device double[ncell][n_in];
+ * lambda_in: host double[n_in] (micron, > 0); mass: device float[ncell];
+ * features: device float[ncell][32]; total: device double[ncell]. */
+int skirt_band_features(const double* absorbed, long long ncell, int n_in, const double* lambda_in,
+                        const float* mass, float* features, double* total, void* stream);
+
+/* The MLP surrogate 32 -> 128 -> 128 -> 100 (SiLU, SiLU, softmax): input
+ * the 32 band features standardised with the training set's mean / std,
+ * output the normalised emission shape, times total(m).  Inference runs on
+ * the tensor cores with BF16 weights and activations, FP32 accumulation;
+ * training keeps FP32 master weights.  The network also stores the
+ * per-feature range [lo, hi] of its training inputs (the "hull"). */
+typedef struct skirt_mlp_s* skirt_mlp_t;
+int skirt_mlp_create(skirt_mlp_t* out, uint64_t seed); /* Kaiming-uniform init from seed */
+int skirt_mlp_destroy(skirt_mlp_t net);
+/* Host float arrays: params[SKIRT_MLP_NPARAM], x_mean/x_std/hull_lo/hull_hi[32]; any may be NULL. */
+int skirt_mlp_set_params(skirt_mlp_t net, const float* params, const float* x_mean, const float* x_std,
+                         const float* hull_lo, const float* hull_hi);
+int skirt_mlp_get_params(skirt_mlp_t net, float* params, float* x_mean, float* x_std, float* hull_lo,
+                         float* hull_hi);
+
+typedef struct {
+    int epochs;          /* passes over the training set (default 20) */
+    int batch;           /* samples per Adam step (default 4096) */
+    float lr;            /* Adam step size (default 2e-3, cosine-decayed to lr/20) */
+    float beta1, beta2, eps; /* Adam moments (defaults 0.9, 0.999, 1e-8) */
+    uint64_t seed;       /* batch order */
+} skirt_mlp_train_opts;
+int skirt_mlp_train_opts_default(skirt_mlp_train_opts* opts);
+
+/* Trains on n samples: features (device float[n][32], raw band features)
+ * and target (device float[n][100], emission shapes summing to 1) with the
+ * cross-entropy loss -sum_l t_l log p_l.  Sets the standardisation and the
+ * hull from the training features.  loss_history: host float[epochs] (mean
+ * loss per epoch) or NULL. */
+int skirt_mlp_train(skirt_mlp_t net, const float* features, const float* target, long long n,
+                    const skirt_mlp_train_opts* opts, float* loss_history, void* stream);
+
+/* One batch of the training arithmetic (FP32): loss and gradient of the
+ * mean cross-entropy with respect to the packed FP32 parameters, for the
+ * standardised inputs x_std (device float[n][32]) -> grad: host float[SKIRT_MLP_NPARAM]. */
+int skirt_mlp_grad(skirt_mlp_t net, const float* x_std, const float* target, int n, float* grad, float* loss,
+                   void* stream);
+
+/* Tensor-core inference: emission (device double[n][100]) = softmax(MLP(
+ * (features - mean) / std)) * total (device double[n]).  If flags is not
+ * NULL (device unsigned char[n]) it receives 1 for rows outside the hull. */
+int skirt_mlp_forward(skirt_mlp_t net, const float* features, const double* total, long long n,
+                      double* emission, unsigned char* flags, void* stream);
+
+typedef struct {
+    unsigned long long n_cells;     /* cells processed */
+    unsigned long long n_fallback;  /* surrogate mode: cells sent to the exact solver */
+    float ms_features, ms_surrogate, ms_exact; /* device time of the three stages */
+} skirt_emission_stats;
+
+/* Emission of every cell from its absorbed spectrum.  mode EXACT: the FP64
+ * solver on every cell.  mode SURROGATE: band features -> MLP on every cell,
+ * then the exact solver overwrites the rows whose features fall outside the
+ * network's hull (net required).  absorbed: device double[ncell][n_in];
+ * lambda_in: host double[n_in]; mass: device float[ncell]; emission: device
+ * double[ncell][100]; temperature: device float[ncell][3] or NULL (exact rows
+ * only; 0 for surrogate rows); stats: host or NULL. */
+int skirt_dust_emission(const double* absorbed, long long ncell, int n_in, const double* lambda_in,
+                        const float* mass, int mode, skirt_mlp_t net, double* emission, float* temperature,
+                        skirt_emission_stats* stats, void* stream);
+
 /* Microbenchmarks for the rooflines of the trace kernel (no counterpart in
  * the paper, which ran on CPUs): kind 0 FP64 FMA rate, 1 FP32 FMA rate,
  * 2 FP32<->FP64 conversion rate, 3 random-address red.global.add.f64 into a

@@ -1,0 +1,437 @@
+// Dust emission step (Sect. 3.2, dust emission phases; Sect. 1, instantaneous
+// dust emission): per-cell emission spectra from the absorbed spectra.
+//
+//  * dust_mass_kernel      M = kappa*rho * cell volume
+//  * band_features_kernel  32 log-spaced band sums per unit mass (log10) and
+//                          the total absorbed power, one thread per cell
+//  * exact_kernel          FP64 equilibrium temperatures of three grain
+//                          populations by bracketed Newton on ln T, then the
+//                          energy-conserving emission spectrum
+// and skirt_dust_emission, which runs either the exact solver on every cell
+// or the MLP surrogate (mlp.cu) with the exact solver as the fallback for
+// cells outside the network's training hull.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "skirt_internal.cuh"
+
+namespace skirt {
+namespace {
+
+constexpr int NOUT = SKIRT_NEMIT;
+constexpr int NB = SKIRT_NBANDS;
+constexpr int NPOP = 3;
+constexpr double T_REF = 30.0, T_LO = 3.0, T_HI = 2000.0;
+const double DELTA[NPOP] = {-0.5, 0.0, 0.5};
+const double BETA[NPOP] = {1.5, 2.0, 2.0};
+// h c / k_B in micron kelvin from the exact SI constants
+const double HCK_UM = 6.62607015e-34 * 299792458.0 / 1.380649e-23 * 1e6;
+
+__constant__ double c_a[NOUT];          // hc/(k lambda_l)
+__constant__ double c_K[NPOP][NOUT];    // W_l kappa_i(lambda_l) lambda_l^-5
+__constant__ double c_lnc[NPOP];        // ln c_i = -ln G_i(30 K)
+__constant__ double c_lnG_lo[NPOP];     // ln G_i(3 K)
+__constant__ double c_lnG_hi[NPOP];     // ln G_i(2000 K)
+__constant__ double c_beta[NPOP];
+
+struct HostModel {
+    double lam[NOUT], W[NOUT], a[NOUT], K[NPOP][NOUT];
+    double lnc[NPOP], lnG_lo[NPOP], lnG_hi[NPOP];
+};
+
+double host_G(const HostModel& h, int i, double T)
+{
+    double g = 0.0;
+    for (int l = 0; l < NOUT; ++l) g += h.K[i][l] / std::expm1(h.a[l] / T);
+    return g;
+}
+
+const HostModel& host_model()
+{
+    static HostModel h;
+    static bool ready = false;
+    if (!ready) {
+        for (int l = 0; l < NOUT; ++l)  // log-spaced 1 .. 1000 micron
+            h.lam[l] = std::pow(10.0, 3.0 * (double)l / (double)(NOUT - 1));
+        for (int l = 0; l < NOUT; ++l) {
+            const double left = l > 0 ? h.lam[l] - h.lam[l - 1] : 0.0;
+            const double right = l < NOUT - 1 ? h.lam[l + 1] - h.lam[l] : 0.0;
+            h.W[l] = 0.5 * (left + right);
+            h.a[l] = HCK_UM / h.lam[l];
+            for (int i = 0; i < NPOP; ++i)
+                h.K[i][l] = h.W[l] * std::pow(h.lam[l] / 100.0, -BETA[i]) * std::pow(h.lam[l], -5.0);
+        }
+        for (int i = 0; i < NPOP; ++i) {
+            h.lnc[i] = -std::log(host_G(h, i, T_REF));
+            h.lnG_lo[i] = std::log(host_G(h, i, T_LO));
+            h.lnG_hi[i] = std::log(host_G(h, i, T_HI));
+        }
+        ready = true;
+    }
+    return h;
+}
+
+cudaError_t upload_model(cudaStream_t s)
+{
+    const HostModel& h = host_model();
+    cudaError_t e;
+    if ((e = cudaMemcpyToSymbolAsync(c_a, h.a, sizeof h.a, 0, cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyToSymbolAsync(c_K, h.K, sizeof h.K, 0, cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyToSymbolAsync(c_lnc, h.lnc, sizeof h.lnc, 0, cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyToSymbolAsync(c_lnG_lo, h.lnG_lo, sizeof h.lnG_lo, 0, cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyToSymbolAsync(c_lnG_hi, h.lnG_hi, sizeof h.lnG_hi, 0, cudaMemcpyHostToDevice, s))) return e;
+    return cudaMemcpyToSymbolAsync(c_beta, BETA, sizeof BETA, 0, cudaMemcpyHostToDevice, s);
+}
+
+__global__ void dust_mass_kernel(const float* __restrict__ kr, long long n, float vol, float* __restrict__ mass)
+{
+    for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (long long)gridDim.x * blockDim.x)
+        mass[m] = kr[m] * vol;
+}
+
+// band b covers the input wavelengths [start[b], start[b+1]) (sorted input grid)
+__global__ void band_features_kernel(const double* __restrict__ A, long long ncell, int n_in,
+                                     const int* __restrict__ start, const float* __restrict__ mass,
+                                     float* __restrict__ features, double* __restrict__ total)
+{
+    __shared__ int s_start[NB + 1];
+    for (int b = threadIdx.x; b <= NB; b += blockDim.x) s_start[b] = start[b];
+    __syncthreads();
+    for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < ncell;
+         m += (long long)gridDim.x * blockDim.x) {
+        const double* row = A + (size_t)m * n_in;
+        const double M = (double)mass[m];
+        double tot = 0.0;
+        for (int b = 0; b < NB; ++b) {
+            double s = 0.0;
+            for (int j = s_start[b]; j < s_start[b + 1]; ++j) s += row[j];
+            tot += s;
+            const double pm = M > 0.0 ? s / M : 0.0;
+            features[(size_t)m * NB + b] = log10f(fmaxf((float)fmax(pm, 1e-30), 1e-30f));
+        }
+        total[m] = tot;
+    }
+}
+
+// G_i(T) = sum_l K_il / expm1(a_l / T) and T dG/dT = sum K_il q x (1 + q)
+__device__ void pop_G(int i, double T, double& G, double& D)
+{
+    G = 0.0;
+    D = 0.0;
+    for (int l = 0; l < NOUT; ++l) {
+        const double x = c_a[l] / T;
+        if (x > 700.0) continue;  // e^x overflows; the term is below 1e-300 of the largest
+        const double q = 1.0 / expm1(x);
+        const double t = c_K[i][l] * q;
+        G += t;
+        D += t * x * (1.0 + q);
+    }
+}
+
+__device__ double solve_T(int i, double ln_ratio)
+{
+    const double target = ln_ratio - c_lnc[i];  // ln G at the solution
+    if (c_lnG_lo[i] - target >= 0.0) return T_LO;
+    if (c_lnG_hi[i] - target <= 0.0) return T_HI;
+    double lo = log(T_LO), hi = log(T_HI);
+    // G ~ T^(4+beta) on the Rayleigh-Jeans side of the grid: first guess
+    double y = log(T_REF) + ln_ratio / (4.0 + c_beta[i]);
+    if (!(y > lo && y < hi)) y = 0.5 * (lo + hi);
+    for (int it = 0; it < 100; ++it) {
+        double G, D;
+        pop_G(i, exp(y), G, D);
+        const double f = log(G) - target;
+        if (f < 0.0) lo = y; else hi = y;
+        double y_new = y - f * G / D;
+        if (!(y_new > lo && y_new < hi)) y_new = 0.5 * (lo + hi);
+        const bool done = fabs(y_new - y) <= 1e-13 * fabs(y);
+        y = y_new;
+        if (done) break;
+    }
+    return exp(y);
+}
+
+// Exact emission for rows m = rows ? rows[k] : k, k < nrows.
+__global__ void exact_kernel(const double* __restrict__ A, int n_in, const double* __restrict__ w,
+                             const float* __restrict__ mass, const unsigned* __restrict__ rows,
+                             long long nrows, double* __restrict__ emission, float* __restrict__ temperature)
+{
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nrows;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long m = rows ? (long long)rows[k] : k;
+        const double* row = A + (size_t)m * n_in;
+        double P[NPOP] = {0.0, 0.0, 0.0};
+        for (int j = 0; j < n_in; ++j) {
+            const double a = row[j];
+            P[0] += __ldg(w + j) * a;
+            P[1] += __ldg(w + n_in + j) * a;
+            P[2] += __ldg(w + 2 * n_in + j) * a;
+        }
+        const double M = (double)mass[m];
+        double T[NPOP], S[NPOP];
+        for (int i = 0; i < NPOP; ++i) {
+            T[i] = 0.0;
+            S[i] = 0.0;
+            if (P[i] > 0.0 && M > 0.0) {
+                T[i] = solve_T(i, log(P[i] / M));
+                double G, D;
+                pop_G(i, T[i], G, D);
+                S[i] = G;
+            }
+        }
+        double* out = emission + (size_t)m * NOUT;
+        for (int l = 0; l < NOUT; ++l) {
+            double e = 0.0;
+            for (int i = 0; i < NPOP; ++i) {
+                if (S[i] > 0.0) {
+                    const double x = c_a[l] / T[i];
+                    if (x <= 700.0) e += P[i] * (c_K[i][l] / expm1(x)) / S[i];
+                }
+            }
+            out[l] = e;
+        }
+        if (temperature)
+            for (int i = 0; i < NPOP; ++i) temperature[(size_t)m * NPOP + i] = (float)T[i];
+    }
+}
+
+__global__ void compact_flags_kernel(const unsigned char* __restrict__ flags, long long n,
+                                     unsigned* __restrict__ rows, unsigned long long* __restrict__ count)
+{
+    for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (long long)gridDim.x * blockDim.x) {
+        const bool f = flags[m] != 0;
+        const unsigned mask = __ballot_sync(__activemask(), f);
+        if (!f) continue;
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(mask) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(mask));
+        base = __shfl_sync(mask, base, leader);
+        rows[base + __popc(mask & ((1u << lane) - 1u))] = (unsigned)m;
+    }
+}
+
+__global__ void zero_temperature_kernel(float* t, long long n)
+{
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        t[k] = 0.f;
+}
+
+int grid_blocks(long long n, int block)
+{
+    long long b = (n + block - 1) / block;
+    if (b > 152LL * 64) b = 152LL * 64;
+    return (int)(b < 1 ? 1 : b);
+}
+
+bool is_device(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int check_lambda(const double* lambda_in, int n_in)
+{
+    if (!lambda_in || n_in < 1 || n_in > 65536) return set_error(SKIRT_ERR_INVALID_ARG, "lambda_in / n_in invalid");
+    for (int j = 0; j < n_in; ++j) {
+        if (!(lambda_in[j] > 0) || !std::isfinite(lambda_in[j]))
+            return set_error(SKIRT_ERR_INVALID_ARG, "lambda_in[%d] must be finite and > 0", j);
+        if (j > 0 && !(lambda_in[j] > lambda_in[j - 1]))
+            return set_error(SKIRT_ERR_INVALID_ARG, "lambda_in must be strictly increasing");
+    }
+    return SKIRT_OK;
+}
+
+// band start indices over a sorted grid: band b = floor(32 ln(l/lmin) / ln(lmax/lmin)) clamped
+std::vector<int> band_starts(const double* lam, int n)
+{
+    std::vector<int> idx(n, 0);
+    const double lo = lam[0], hi = lam[n - 1];
+    for (int j = 0; j < n; ++j) {
+        int b = 0;
+        if (hi > lo) b = (int)std::floor(NB * std::log(lam[j] / lo) / std::log(hi / lo));
+        idx[j] = b < 0 ? 0 : (b > NB - 1 ? NB - 1 : b);
+    }
+    std::vector<int> start(NB + 1, n);
+    for (int b = NB; b >= 0; --b) {
+        int s = n;
+        for (int j = 0; j < n; ++j)
+            if (idx[j] >= b) { s = j; break; }
+        start[b] = b == NB ? n : s;
+    }
+    return start;
+}
+
+std::vector<double> share_table(const double* lam, int n)
+{
+    std::vector<double> w((size_t)NPOP * n);
+    for (int j = 0; j < n; ++j) {
+        double r[NPOP], sum = 0.0;
+        for (int i = 0; i < NPOP; ++i) {
+            r[i] = std::pow(lam[j] / 0.55, DELTA[i]);
+            sum += r[i];
+        }
+        for (int i = 0; i < NPOP; ++i) w[(size_t)i * n + j] = r[i] / sum;
+    }
+    return w;
+}
+
+#define ECK(call)                                                                                       \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return set_error(e_ == cudaErrorMemoryAllocation ? SKIRT_ERR_OOM : SKIRT_ERR_CUDA,          \
+                             "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+}  // namespace
+
+int launch_exact_emission(const double* absorbed, int n_in, const double* w_dev, const float* mass,
+                          const unsigned* rows, long long nrows, double* emission, float* temperature,
+                          cudaStream_t s)
+{
+    ECK(upload_model(s));
+    if (nrows > 0) exact_kernel<<<grid_blocks(nrows, 128), 128, 0, s>>>(absorbed, n_in, w_dev, mass, rows, nrows,
+                                                                      emission, temperature);
+    ECK(cudaGetLastError());
+    return SKIRT_OK;
+}
+
+}  // namespace skirt
+
+using namespace skirt;
+
+extern "C" int skirt_emission_grid(double* lambda_um, double* weights)
+{
+    const HostModel& h = host_model();
+    if (lambda_um) std::memcpy(lambda_um, h.lam, sizeof h.lam);
+    if (weights) std::memcpy(weights, h.W, sizeof h.W);
+    return SKIRT_OK;
+}
+
+extern "C" int skirt_dust_mass(skirt_grid_t g, float* mass, void* stream)
+{
+    if (!g || !mass) return set_error(SKIRT_ERR_INVALID_ARG, "grid / mass is NULL");
+    if (!is_device(mass)) return set_error(SKIRT_ERR_INVALID_ARG, "mass must be device memory");
+    const double vol = (g->bbox[1] - g->bbox[0]) / g->nx * (g->bbox[3] - g->bbox[2]) / g->ny *
+                       (g->bbox[5] - g->bbox[4]) / g->nz;
+    dust_mass_kernel<<<grid_blocks(g->ncell, 256), 256, 0, (cudaStream_t)stream>>>(g->kr32, g->ncell, (float)vol, mass);
+    ECK(cudaGetLastError());
+    ECK(cudaStreamSynchronize((cudaStream_t)stream));
+    return SKIRT_OK;
+}
+
+extern "C" int skirt_band_features(const double* absorbed, long long ncell, int n_in, const double* lambda_in,
+                                   const float* mass, float* features, double* total, void* stream)
+{
+    if (ncell < 0) return set_error(SKIRT_ERR_INVALID_ARG, "ncell < 0");
+    if (int r = check_lambda(lambda_in, n_in)) return r;
+    if (ncell == 0) return SKIRT_OK;
+    if (!is_device(absorbed) || !is_device(mass) || !is_device(features) || !is_device(total))
+        return set_error(SKIRT_ERR_INVALID_ARG, "absorbed / mass / features / total must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int> start = band_starts(lambda_in, n_in);
+    int* d_start = nullptr;
+    ECK(cudaMallocAsync((void**)&d_start, sizeof(int) * (NB + 1), s));
+    ECK(cudaMemcpyAsync(d_start, start.data(), sizeof(int) * (NB + 1), cudaMemcpyHostToDevice, s));
+    band_features_kernel<<<grid_blocks(ncell, 128), 128, 0, s>>>(absorbed, ncell, n_in, d_start, mass, features, total);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(d_start, s);
+    if (e != cudaSuccess) return set_error(SKIRT_ERR_CUDA, "band features: %s", cudaGetErrorString(e));
+    ECK(cudaStreamSynchronize(s));
+    return SKIRT_OK;
+}
+
+extern "C" int skirt_dust_emission(const double* absorbed, long long ncell, int n_in, const double* lambda_in,
+                                   const float* mass, int mode, skirt_mlp_t net, double* emission, float* temperature,
+                                   skirt_emission_stats* stats, void* stream)
+{
+    if (ncell < 0) return set_error(SKIRT_ERR_INVALID_ARG, "ncell < 0");
+    if (int r = check_lambda(lambda_in, n_in)) return r;
+    if (mode != SKIRT_EMIT_EXACT && mode != SKIRT_EMIT_SURROGATE)
+        return set_error(SKIRT_ERR_INVALID_ARG, "unknown mode %d", mode);
+    if (mode == SKIRT_EMIT_SURROGATE && !net) return set_error(SKIRT_ERR_INVALID_ARG, "surrogate mode needs a network");
+    if (stats) std::memset(stats, 0, sizeof *stats);
+    if (ncell == 0) return SKIRT_OK;
+    if (ncell >= (1ll << 32)) return set_error(SKIRT_ERR_INVALID_ARG, "ncell must be < 2^32");
+    if (!is_device(absorbed) || !is_device(mass) || !is_device(emission) || (temperature && !is_device(temperature)))
+        return set_error(SKIRT_ERR_INVALID_ARG, "absorbed / mass / emission / temperature must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<double> w = share_table(lambda_in, n_in);
+    double* d_w = nullptr;
+    ECK(cudaMallocAsync((void**)&d_w, sizeof(double) * w.size(), s));
+    ECK(cudaMemcpyAsync(d_w, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice, s));
+    cudaEvent_t ev[4];
+    for (auto& e : ev) ECK(cudaEventCreate(&e));
+    int rc = SKIRT_OK;
+    unsigned long long nfb = 0;
+    if (mode == SKIRT_EMIT_EXACT) {
+        ECK(cudaEventRecord(ev[0], s));
+        rc = launch_exact_emission(absorbed, n_in, d_w, mass, nullptr, ncell, emission, temperature, s);
+        ECK(cudaEventRecord(ev[1], s));
+    } else {
+        float* d_feat = nullptr;
+        double* d_tot = nullptr;
+        unsigned char* d_flag = nullptr;
+        unsigned* d_rows = nullptr;
+        unsigned long long* d_cnt = nullptr;
+        ECK(cudaMallocAsync((void**)&d_feat, sizeof(float) * NB * (size_t)ncell, s));
+        ECK(cudaMallocAsync((void**)&d_tot, sizeof(double) * (size_t)ncell, s));
+        ECK(cudaMallocAsync((void**)&d_flag, (size_t)ncell, s));
+        ECK(cudaMallocAsync((void**)&d_rows, sizeof(unsigned) * (size_t)ncell, s));
+        ECK(cudaMallocAsync((void**)&d_cnt, sizeof(unsigned long long), s));
+        ECK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), s));
+        std::vector<int> start = band_starts(lambda_in, n_in);
+        int* d_start = nullptr;
+        ECK(cudaMallocAsync((void**)&d_start, sizeof(int) * (NB + 1), s));
+        ECK(cudaMemcpyAsync(d_start, start.data(), sizeof(int) * (NB + 1), cudaMemcpyHostToDevice, s));
+        if (temperature) zero_temperature_kernel<<<grid_blocks(3 * ncell, 256), 256, 0, s>>>(temperature, 3 * ncell);
+        ECK(cudaEventRecord(ev[0], s));
+        band_features_kernel<<<grid_blocks(ncell, 128), 128, 0, s>>>(absorbed, ncell, n_in, d_start, mass, d_feat, d_tot);
+        ECK(cudaGetLastError());
+        ECK(cudaEventRecord(ev[1], s));
+        rc = mlp_forward_internal(net, d_feat, d_tot, ncell, emission, d_flag, s);
+        if (rc == SKIRT_OK) {
+            compact_flags_kernel<<<grid_blocks(ncell, 256), 256, 0, s>>>(d_flag, ncell, d_rows, d_cnt);
+            ECK(cudaGetLastError());
+            ECK(cudaEventRecord(ev[2], s));
+            ECK(cudaMemcpyAsync(&nfb, d_cnt, sizeof nfb, cudaMemcpyDeviceToHost, s));
+            ECK(cudaStreamSynchronize(s));
+            rc = launch_exact_emission(absorbed, n_in, d_w, mass, d_rows, (long long)nfb, emission, temperature, s);
+            ECK(cudaEventRecord(ev[3], s));
+        }
+        cudaFreeAsync(d_feat, s);
+        cudaFreeAsync(d_tot, s);
+        cudaFreeAsync(d_flag, s);
+        cudaFreeAsync(d_rows, s);
+        cudaFreeAsync(d_cnt, s);
+        cudaFreeAsync(d_start, s);
+    }
+    cudaFreeAsync(d_w, s);
+    ECK(cudaStreamSynchronize(s));
+    if (stats && rc == SKIRT_OK) {
+        stats->n_cells = (unsigned long long)ncell;
+        stats->n_fallback = nfb;
+        float a = 0.f, b = 0.f, c = 0.f;
+        if (mode == SKIRT_EMIT_EXACT) {
+            cudaEventElapsedTime(&c, ev[0], ev[1]);
+        } else {
+            cudaEventElapsedTime(&a, ev[0], ev[1]);
+            cudaEventElapsedTime(&b, ev[1], ev[2]);
+            cudaEventElapsedTime(&c, ev[2], ev[3]);
+        }
+        stats->ms_features = a;
+        stats->ms_surrogate = b;
+        stats->ms_exact = c;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    return rc;
+}

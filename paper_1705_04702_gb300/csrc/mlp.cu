@@ -1,0 +1,768 @@
+// MLP surrogate of the dust-emission step: 32 band features -> 128 -> 128 ->
+// 100 emission-shape logits (SiLU, SiLU, softmax).
+//
+// Inference (mlp_infer_kernel): one warp per 16 rows, the three layers as
+// BF16 tensor-core products with FP32 accumulation (mma.sync m16n8k16 in
+// inline PTX); weights staged once per block in shared memory; the FP32
+// accumulator fragment of one layer, passed through SiLU and packed to BF16,
+// is exactly the A-operand fragment of the next layer, so activations never
+// leave registers.  Softmax over the 100 outputs is reduced across the four
+// lanes that hold a row; the result times the cell's absorbed power is
+// written as FP64 emission.  The same pass flags rows whose raw features
+// leave the training hull.
+//
+// Training (skirt_mlp_train): FP32 master weights, tiled FP32 GEMMs,
+// explicit backward pass (softmax cross-entropy, SiLU'), Adam with cosine
+// step decay.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "skirt_internal.cuh"
+
+namespace skirt {
+namespace {
+
+constexpr int NIN = SKIRT_NBANDS;      // 32
+constexpr int NH = SKIRT_MLP_HIDDEN;   // 128
+constexpr int NO = SKIRT_NEMIT;        // 100
+constexpr int NO_PAD = 104;            // 13 n-tiles of 8
+constexpr int NPARAM = SKIRT_MLP_NPARAM;
+constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + NH * NIN, OFF_W2 = OFF_B1 + NH, OFF_B2 = OFF_W2 + NH * NH,
+              OFF_W3 = OFF_B2 + NH, OFF_B3 = OFF_W3 + NO * NH;
+static_assert(OFF_B3 + NO == NPARAM, "packed parameter layout");
+
+#define MCK(call)                                                                                       \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return set_error(e_ == cudaErrorMemoryAllocation ? SKIRT_ERR_OOM : SKIRT_ERR_CUDA,          \
+                             "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+// --------------------------------------------------------------------------
+// inference
+// --------------------------------------------------------------------------
+constexpr int INF_WARPS = 4;
+constexpr int INF_ROWS = 16 * INF_WARPS;
+// shared memory: W1 [128][32], W2 [128][128], W3 [104][128] (bf16), biases
+// [128 + 128 + 104] (fp32), mean / inv_std / lo / hi [32] each, per-warp
+// feature staging [16][32] fp32
+constexpr size_t SM_W1 = 0;
+constexpr size_t SM_W2 = SM_W1 + sizeof(uint16_t) * NH * NIN;
+constexpr size_t SM_W3 = SM_W2 + sizeof(uint16_t) * NH * NH;
+constexpr size_t SM_B = SM_W3 + sizeof(uint16_t) * NO_PAD * NH;
+constexpr size_t SM_ST = SM_B + sizeof(float) * (NH + NH + NO_PAD);
+constexpr size_t SM_X = SM_ST + sizeof(float) * 4 * NIN;
+constexpr size_t SM_TOTAL = SM_X + sizeof(float) * INF_WARPS * 16 * NIN;
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float* c, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.f + __expf(-z)); }
+
+// acc[j][0..3] for n-tiles j: rows (g, g+8), cols 8j + 2t + {0,1}; produces
+// the next layer's A fragments: k-tile kk from n-tiles 2kk, 2kk+1
+template <int NT>
+__device__ __forceinline__ void to_afrag(const float (&acc)[NT][4], uint32_t (&a)[NT / 2][4])
+{
+#pragma unroll
+    for (int kk = 0; kk < NT / 2; ++kk) {
+        a[kk][0] = pack_bf16(silu_f(acc[2 * kk][0]), silu_f(acc[2 * kk][1]));
+        a[kk][1] = pack_bf16(silu_f(acc[2 * kk][2]), silu_f(acc[2 * kk][3]));
+        a[kk][2] = pack_bf16(silu_f(acc[2 * kk + 1][0]), silu_f(acc[2 * kk + 1][1]));
+        a[kk][3] = pack_bf16(silu_f(acc[2 * kk + 1][2]), silu_f(acc[2 * kk + 1][3]));
+    }
+}
+
+// one layer: out[NT] n-tiles = A (KT k-tiles) x W^T, W [rows = 8*NT][cols = 16*KT] bf16 in smem
+template <int NT, int KT>
+__device__ __forceinline__ void layer(const uint32_t (&a)[KT][4], const uint16_t* __restrict__ W,
+                                      const float* __restrict__ bias, float (&out)[NT][4], int g, int t)
+{
+    constexpr int K = 16 * KT;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        const float b0 = bias[8 * j + 2 * t], b1 = bias[8 * j + 2 * t + 1];
+        out[j][0] = b0; out[j][1] = b1; out[j][2] = b0; out[j][3] = b1;
+        const uint16_t* wr = W + (size_t)(8 * j + g) * K + 2 * t;
+#pragma unroll
+        for (int kk = 0; kk < KT; ++kk) {
+            const uint32_t b0w = *reinterpret_cast<const uint32_t*>(wr + 16 * kk);
+            const uint32_t b1w = *reinterpret_cast<const uint32_t*>(wr + 16 * kk + 8);
+            mma_bf16(out[j], a[kk][0], a[kk][1], a[kk][2], a[kk][3], b0w, b1w);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(32 * INF_WARPS) mlp_infer_kernel(
+    const uint16_t* __restrict__ Wg, const float* __restrict__ Bg, const float* __restrict__ stats,
+    const float* __restrict__ features, const double* __restrict__ total, long long n,
+    double* __restrict__ emission, unsigned char* __restrict__ flags)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    // stage the weights (bf16, contiguous W1 W2 W3) and biases / statistics
+    {
+        const int nw = (NH * NIN + NH * NH + NO_PAD * NH) / 8;  // 16-byte chunks
+        const uint4* src = reinterpret_cast<const uint4*>(Wg);
+        uint4* dst = reinterpret_cast<uint4*>(sm + SM_W1);
+        for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
+        float* sb = reinterpret_cast<float*>(sm + SM_B);
+        for (int i = threadIdx.x; i < NH + NH + NO_PAD; i += blockDim.x) sb[i] = Bg[i];
+        float* ss = reinterpret_cast<float*>(sm + SM_ST);
+        for (int i = threadIdx.x; i < 4 * NIN; i += blockDim.x) ss[i] = stats[i];
+    }
+    __syncthreads();
+    const uint16_t* W1 = reinterpret_cast<const uint16_t*>(sm + SM_W1);
+    const uint16_t* W2 = reinterpret_cast<const uint16_t*>(sm + SM_W2);
+    const uint16_t* W3 = reinterpret_cast<const uint16_t*>(sm + SM_W3);
+    const float* B1 = reinterpret_cast<const float*>(sm + SM_B);
+    const float* B2 = B1 + NH;
+    const float* B3 = B2 + NH;
+    const float* mean = reinterpret_cast<const float*>(sm + SM_ST);
+    const float* istd = mean + NIN;
+    const float* hlo = istd + NIN;
+    const float* hhi = hlo + NIN;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    float* xs = reinterpret_cast<float*>(sm + SM_X) + warp * 16 * NIN;
+
+    for (long long base = (long long)blockIdx.x * INF_ROWS + warp * 16; base < n;
+         base += (long long)gridDim.x * INF_ROWS) {
+        // ---- features of 16 rows: coalesced load, hull check, standardise
+        for (int i = lane; i < 16 * NIN; i += 32) {
+            const long long r = base + i / NIN;
+            xs[i] = r < n ? features[r * NIN + (i % NIN)] : 0.f;
+        }
+        __syncwarp();
+        if (lane < 16 && flags) {
+            const long long r = base + lane;
+            if (r < n) {
+                bool out = false;
+                for (int k = 0; k < NIN; ++k) {
+                    const float v = xs[lane * NIN + k];
+                    out |= !(v >= hlo[k] && v <= hhi[k]);
+                }
+                flags[r] = out ? 1 : 0;
+            }
+        }
+        uint32_t a1[2][4];
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+            const int c = 16 * kk + 2 * t;
+            auto sx = [&](int row, int col) { return (xs[row * NIN + col] - mean[col]) * istd[col]; };
+            a1[kk][0] = pack_bf16(sx(g, c), sx(g, c + 1));
+            a1[kk][1] = pack_bf16(sx(g + 8, c), sx(g + 8, c + 1));
+            a1[kk][2] = pack_bf16(sx(g, c + 8), sx(g, c + 9));
+            a1[kk][3] = pack_bf16(sx(g + 8, c + 8), sx(g + 8, c + 9));
+        }
+        __syncwarp();
+        // ---- layers
+        float h[NH / 8][4];
+        layer<NH / 8, 2>(a1, W1, B1, h, g, t);
+        uint32_t a2[NH / 16][4];
+        to_afrag<NH / 8>(h, a2);
+        layer<NH / 8, NH / 16>(a2, W2, B2, h, g, t);
+        to_afrag<NH / 8>(h, a2);
+        float z[NO_PAD / 8][4];
+        layer<NO_PAD / 8, NH / 16>(a2, W3, B3, z, g, t);
+        // ---- softmax over the 100 outputs of rows g and g+8 (4 lanes per row)
+        float m0 = -3.0e38f, m1 = -3.0e38f;
+#pragma unroll
+        for (int j = 0; j < NO_PAD / 8; ++j) {
+            if (8 * j + 2 * t < NO) { m0 = fmaxf(m0, fmaxf(z[j][0], z[j][1])); m1 = fmaxf(m1, fmaxf(z[j][2], z[j][3])); }
+        }
+        m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, 1));
+        m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, 2));
+        m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, 1));
+        m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, 2));
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int j = 0; j < NO_PAD / 8; ++j) {
+            const bool ok = 8 * j + 2 * t < NO;
+            z[j][0] = ok ? __expf(z[j][0] - m0) : 0.f;
+            z[j][1] = ok ? __expf(z[j][1] - m0) : 0.f;
+            z[j][2] = ok ? __expf(z[j][2] - m1) : 0.f;
+            z[j][3] = ok ? __expf(z[j][3] - m1) : 0.f;
+            s0 += z[j][0] + z[j][1];
+            s1 += z[j][2] + z[j][3];
+        }
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+        const long long r0 = base + g, r1 = base + g + 8;
+        const double f0 = r0 < n ? total[r0] / (double)s0 : 0.0;
+        const double f1 = r1 < n ? total[r1] / (double)s1 : 0.0;
+#pragma unroll
+        for (int j = 0; j < NO_PAD / 8; ++j) {
+            const int c = 8 * j + 2 * t;
+            if (c < NO) {
+                if (r0 < n)
+                    *reinterpret_cast<double2*>(emission + r0 * NO + c) =
+                        make_double2(f0 * (double)z[j][0], f0 * (double)z[j][1]);
+                if (r1 < n)
+                    *reinterpret_cast<double2*>(emission + r1 * NO + c) =
+                        make_double2(f1 * (double)z[j][2], f1 * (double)z[j][3]);
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// training kernels (FP32)
+// --------------------------------------------------------------------------
+// C[M][N] = op(A)[M][K] op(B)[K][N]; A is [M][K] (ta = 0) or [K][M] (ta = 1);
+// B is [K][N] (tb = 0) or [N][K] (tb = 1); all row-major.  64 x 64 tiles,
+// 256 threads, 4 x 4 outputs each.
+__global__ void gemm_kernel(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ C, int M,
+                            int N, int K, int ta, int tb)
+{
+    __shared__ float As[16][65], Bs[16][65];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int i = threadIdx.x; i < 16 * 64; i += 256) {
+            const int kk = i / 64, mm = i % 64;
+            const int gm = m0 + mm, gk = k0 + kk;
+            As[kk][mm] = (gm < M && gk < K) ? (ta ? A[(size_t)gk * M + gm] : A[(size_t)gm * K + gk]) : 0.f;
+            const int gn = n0 + mm;
+            Bs[kk][mm] = (gn < N && gk < K) ? (tb ? B[(size_t)gn * K + gk] : B[(size_t)gk * N + gn]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { a[i] = As[kk][ty + 16 * i]; b[i] = Bs[kk][tx + 16 * i]; }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
+            if (gm < M && gn < N) C[(size_t)gm * N + gn] = acc[i][j];
+        }
+}
+
+// z += bias (per column); a = silu(z)
+__global__ void bias_silu_kernel(float* z, float* a, const float* bias, int rows, int cols)
+{
+    const long long n = (long long)rows * cols;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float v = z[i] + bias[i % cols];
+        z[i] = v;
+        a[i] = v / (1.f + expf(-v));
+    }
+}
+
+// d = da * silu'(z)
+__global__ void silu_back_kernel(const float* z, const float* da, float* d, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float s = 1.f / (1.f + expf(-z[i]));
+        d[i] = da[i] * s * (1.f + z[i] * (1.f - s));
+    }
+}
+
+// per row: p = softmax(z + b3); loss += -sum t log p; dz = (p - t) / rows  (one warp per row)
+__global__ void softmax_xent_kernel(const float* z, const float* bias, const float* target, float* dz, int rows,
+                                    float* loss)
+{
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= rows) return;
+    const float* zr = z + (size_t)warp * NO;
+    const float* tr = target + (size_t)warp * NO;
+    float v[4], m = -3.0e38f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int c = lane + 32 * k;
+        v[k] = c < NO ? zr[c] + bias[c] : -3.0e38f;
+        m = fmaxf(m, v[k]);
+    }
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s += (lane + 32 * k < NO) ? expf(v[k] - m) : 0.f;
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const float ls = logf(s);
+    float l = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int c = lane + 32 * k;
+        if (c < NO) {
+            const float logp = v[k] - m - ls;
+            l -= tr[c] * logp;
+            dz[(size_t)warp * NO + c] = (expf(logp) - tr[c]) / (float)rows;
+        }
+    }
+    for (int o = 16; o; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if (lane == 0) atomicAdd(loss, l / (float)rows);
+}
+
+// out[c] = sum over rows of d[r][c]
+__global__ void colsum_kernel(const float* d, float* out, int rows, int cols)
+{
+    const int c = blockIdx.x;
+    float s = 0.f;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) s += d[(size_t)r * cols + c];
+    __shared__ float red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = red[0];
+}
+
+__global__ void adam_kernel(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2,
+                            float eps, float c1, float c2)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// batch gather with an affine permutation of the sample indices, standardising the features
+__global__ void gather_kernel(const float* __restrict__ feat, const float* __restrict__ target, long long n,
+                              long long first, unsigned long long a, unsigned long long b, int rows,
+                              const float* __restrict__ stats, float* __restrict__ xb, float* __restrict__ tb)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows * (NIN + NO); i += gridDim.x * blockDim.x) {
+        const int r = i / (NIN + NO), c = i % (NIN + NO);
+        const unsigned long long src = (a * (unsigned long long)(first + r) + b) % (unsigned long long)n;
+        if (c < NIN) xb[(size_t)r * NIN + c] = (feat[src * NIN + c] - stats[c]) * stats[NIN + c];
+        else tb[(size_t)r * NO + (c - NIN)] = target[src * NO + (c - NIN)];
+    }
+}
+
+// per-feature sums over n samples: sum, sum of squares, min, max (one block per feature)
+__global__ void feature_stats_kernel(const float* feat, long long n, double* out)
+{
+    const int c = blockIdx.x;
+    double s = 0.0, s2 = 0.0;
+    float lo = 3.0e38f, hi = -3.0e38f;
+    for (long long r = threadIdx.x; r < n; r += blockDim.x) {
+        const float v = feat[r * NIN + c];
+        s += v;
+        s2 += (double)v * v;
+        lo = fminf(lo, v);
+        hi = fmaxf(hi, v);
+    }
+    __shared__ double rs[256], rs2[256];
+    __shared__ float rl[256], rh[256];
+    rs[threadIdx.x] = s; rs2[threadIdx.x] = s2; rl[threadIdx.x] = lo; rh[threadIdx.x] = hi;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+        if (threadIdx.x < o) {
+            rs[threadIdx.x] += rs[threadIdx.x + o];
+            rs2[threadIdx.x] += rs2[threadIdx.x + o];
+            rl[threadIdx.x] = fminf(rl[threadIdx.x], rl[threadIdx.x + o]);
+            rh[threadIdx.x] = fmaxf(rh[threadIdx.x], rh[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[4 * c + 0] = rs[0];
+        out[4 * c + 1] = rs2[0];
+        out[4 * c + 2] = rl[0];
+        out[4 * c + 3] = rh[0];
+    }
+}
+
+// bf16 copies of the weights (W3 padded to 104 rows with zeros) and the fp32
+// biases (b3 padded with -inf-like values so that padded logits vanish)
+__global__ void pack_inference_kernel(const float* __restrict__ P, uint16_t* __restrict__ W, float* __restrict__ B)
+{
+    const int nW = NH * NIN + NH * NH + NO_PAD * NH;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nW; i += gridDim.x * blockDim.x) {
+        float v;
+        if (i < NH * NIN) v = P[OFF_W1 + i];
+        else if (i < NH * NIN + NH * NH) v = P[OFF_W2 + (i - NH * NIN)];
+        else {
+            const int k = i - NH * NIN - NH * NH;
+            v = k < NO * NH ? P[OFF_W3 + k] : 0.f;
+        }
+        __nv_bfloat16 b = __float2bfloat16_rn(v);
+        W[i] = *reinterpret_cast<uint16_t*>(&b);
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NH + NH + NO_PAD; i += gridDim.x * blockDim.x) {
+        if (i < NH) B[i] = P[OFF_B1 + i];
+        else if (i < 2 * NH) B[i] = P[OFF_B2 + i - NH];
+        else B[i] = (i - 2 * NH) < NO ? P[OFF_B3 + i - 2 * NH] : -1.0e30f;
+    }
+}
+
+int blocks_for(long long n, int block)
+{
+    long long b = (n + block - 1) / block;
+    if (b > 4096) b = 4096;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// splitmix64: the library's host-side generator for the initial weights
+uint64_t splitmix64(uint64_t& s)
+{
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+}  // namespace skirt
+
+using namespace skirt;
+
+struct skirt_mlp_s {
+    float* P = nullptr;        // FP32 master parameters [NPARAM]
+    float* G = nullptr;        // gradient [NPARAM]
+    float* Mo = nullptr;       // Adam first moment
+    float* Vo = nullptr;       // Adam second moment
+    uint16_t* Wb = nullptr;    // bf16 weights for inference
+    float* Bb = nullptr;       // fp32 biases for inference (b3 padded)
+    float* stats = nullptr;    // device: mean[32], 1/std[32], lo[32], hi[32]
+    float host_stats[4 * NIN]; // mean, std, lo, hi
+    bool packed = false;
+};
+
+namespace skirt {
+
+static int upload_stats(skirt_mlp_s* net)
+{
+    float d[4 * NIN];
+    for (int k = 0; k < NIN; ++k) {
+        d[k] = net->host_stats[k];
+        d[NIN + k] = 1.f / net->host_stats[NIN + k];
+        d[2 * NIN + k] = net->host_stats[2 * NIN + k];
+        d[3 * NIN + k] = net->host_stats[3 * NIN + k];
+    }
+    MCK(cudaMemcpy(net->stats, d, sizeof d, cudaMemcpyHostToDevice));
+    return SKIRT_OK;
+}
+
+static int repack(skirt_mlp_s* net, cudaStream_t s)
+{
+    pack_inference_kernel<<<64, 256, 0, s>>>(net->P, net->Wb, net->Bb);
+    MCK(cudaGetLastError());
+    net->packed = true;
+    return SKIRT_OK;
+}
+
+int mlp_forward_internal(skirt_mlp_s* net, const float* features, const double* total, long long n, double* emission,
+                         unsigned char* flags, cudaStream_t s)
+{
+    if (!net->packed) {
+        int r = repack(net, s);
+        if (r) return r;
+    }
+    MCK(cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_TOTAL));
+    int sms = 0, dev = 0, per_sm = 0;
+    MCK(cudaGetDevice(&dev));
+    MCK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    MCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_infer_kernel, 32 * INF_WARPS, SM_TOTAL));
+    long long tiles = (n + INF_ROWS - 1) / INF_ROWS;
+    long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    if (grid > tiles) grid = tiles;
+    if (grid < 1) grid = 1;
+    mlp_infer_kernel<<<(int)grid, 32 * INF_WARPS, SM_TOTAL, s>>>(net->Wb, net->Bb, net->stats, features, total, n,
+                                                                  emission, flags);
+    MCK(cudaGetLastError());
+    return SKIRT_OK;
+}
+
+}  // namespace skirt
+
+// ---------------------------------------------------------------- C ABI
+extern "C" int skirt_mlp_create(skirt_mlp_t* out, uint64_t seed)
+{
+    if (!out) return set_error(SKIRT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    skirt_mlp_s* net = new skirt_mlp_s;
+    auto bail = [&](int code) {
+        skirt_mlp_destroy(net);
+        return code;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&net->P, sizeof(float) * NPARAM)) || (e = cudaMalloc(&net->G, sizeof(float) * NPARAM)) ||
+        (e = cudaMalloc(&net->Mo, sizeof(float) * NPARAM)) || (e = cudaMalloc(&net->Vo, sizeof(float) * NPARAM)) ||
+        (e = cudaMalloc(&net->Wb, sizeof(uint16_t) * (NH * NIN + NH * NH + NO_PAD * NH))) ||
+        (e = cudaMalloc(&net->Bb, sizeof(float) * (NH + NH + NO_PAD))) ||
+        (e = cudaMalloc(&net->stats, sizeof(float) * 4 * NIN)))
+        return bail(set_error(SKIRT_ERR_OOM, "mlp buffers: %s", cudaGetErrorString(e)));
+    // Kaiming-uniform weights U(-sqrt(6 / fan_in), +sqrt(6 / fan_in)), zero biases
+    std::vector<float> h(NPARAM, 0.f);
+    uint64_t st = seed;
+    auto fill = [&](int off, int rows, int cols) {
+        const double b = std::sqrt(6.0 / cols);
+        for (int i = 0; i < rows * cols; ++i) {
+            const double u = (double)(splitmix64(st) >> 11) * (1.0 / 9007199254740992.0);
+            h[off + i] = (float)((2.0 * u - 1.0) * b);
+        }
+    };
+    fill(OFF_W1, NH, NIN);
+    fill(OFF_W2, NH, NH);
+    fill(OFF_W3, NO, NH);
+    if ((e = cudaMemcpy(net->P, h.data(), sizeof(float) * NPARAM, cudaMemcpyHostToDevice)))
+        return bail(set_error(SKIRT_ERR_CUDA, "mlp init: %s", cudaGetErrorString(e)));
+    for (int k = 0; k < NIN; ++k) {
+        net->host_stats[k] = 0.f;
+        net->host_stats[NIN + k] = 1.f;
+        net->host_stats[2 * NIN + k] = -3.0e38f;
+        net->host_stats[3 * NIN + k] = 3.0e38f;
+    }
+    if (int r = upload_stats(net)) return bail(r);
+    *out = net;
+    return SKIRT_OK;
+}
+
+extern "C" int skirt_mlp_destroy(skirt_mlp_t net)
+{
+    if (!net) return SKIRT_OK;
+    cudaFree(net->P);
+    cudaFree(net->G);
+    cudaFree(net->Mo);
+    cudaFree(net->Vo);
+    cudaFree(net->Wb);
+    cudaFree(net->Bb);
+    cudaFree(net->stats);
+    delete net;
+    return SKIRT_OK;
+}
+
+extern "C" int skirt_mlp_set_params(skirt_mlp_t net, const float* params, const float* x_mean, const float* x_std,
+                                    const float* hull_lo, const float* hull_hi)
+{
+    if (!net) return set_error(SKIRT_ERR_INVALID_ARG, "net is NULL");
+    if (params) {
+        for (int i = 0; i < NPARAM; ++i)
+            if (!std::isfinite(params[i])) return set_error(SKIRT_ERR_INVALID_ARG, "params[%d] is not finite", i);
+        MCK(cudaMemcpy(net->P, params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice));
+        net->packed = false;
+    }
+    if (x_std)
+        for (int k = 0; k < NIN; ++k)
+            if (!(x_std[k] > 0)) return set_error(SKIRT_ERR_INVALID_ARG, "x_std[%d] must be > 0", k);
+    if (x_mean) std::memcpy(net->host_stats, x_mean, sizeof(float) * NIN);
+    if (x_std) std::memcpy(net->host_stats + NIN, x_std, sizeof(float) * NIN);
+    if (hull_lo) std::memcpy(net->host_stats + 2 * NIN, hull_lo, sizeof(float) * NIN);
+    if (hull_hi) std::memcpy(net->host_stats + 3 * NIN, hull_hi, sizeof(float) * NIN);
+    return upload_stats(net);
+}
+
+extern "C" int skirt_mlp_get_params(skirt_mlp_t net, float* params, float* x_mean, float* x_std, float* hull_lo,
+                                    float* hull_hi)
+{
+    if (!net) return set_error(SKIRT_ERR_INVALID_ARG, "net is NULL");
+    if (params) MCK(cudaMemcpy(params, net->P, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost));
+    if (x_mean) std::memcpy(x_mean, net->host_stats, sizeof(float) * NIN);
+    if (x_std) std::memcpy(x_std, net->host_stats + NIN, sizeof(float) * NIN);
+    if (hull_lo) std::memcpy(hull_lo, net->host_stats + 2 * NIN, sizeof(float) * NIN);
+    if (hull_hi) std::memcpy(hull_hi, net->host_stats + 3 * NIN, sizeof(float) * NIN);
+    return SKIRT_OK;
+}
+
+extern "C" int skirt_mlp_train_opts_default(skirt_mlp_train_opts* o)
+{
+    if (!o) return set_error(SKIRT_ERR_INVALID_ARG, "opts is NULL");
+    o->epochs = 20;
+    o->batch = 4096;
+    o->lr = 2e-3f;
+    o->beta1 = 0.9f;
+    o->beta2 = 0.999f;
+    o->eps = 1e-8f;
+    o->seed = 1;
+    return SKIRT_OK;
+}
+
+namespace {
+
+struct Work {
+    float *xb = nullptr, *tb = nullptr, *z1 = nullptr, *a1 = nullptr, *z2 = nullptr, *a2 = nullptr, *z3 = nullptr,
+          *d3 = nullptr, *da = nullptr, *d = nullptr, *loss = nullptr;
+    cudaError_t alloc(int B, cudaStream_t s)
+    {
+        cudaError_t e;
+        if ((e = cudaMallocAsync((void**)&xb, sizeof(float) * B * NIN, s))) return e;
+        if ((e = cudaMallocAsync((void**)&tb, sizeof(float) * B * NO, s))) return e;
+        if ((e = cudaMallocAsync((void**)&z1, sizeof(float) * B * NH, s))) return e;
+        if ((e = cudaMallocAsync((void**)&a1, sizeof(float) * B * NH, s))) return e;
+        if ((e = cudaMallocAsync((void**)&z2, sizeof(float) * B * NH, s))) return e;
+        if ((e = cudaMallocAsync((void**)&a2, sizeof(float) * B * NH, s))) return e;
+        if ((e = cudaMallocAsync((void**)&z3, sizeof(float) * B * NO, s))) return e;
+        if ((e = cudaMallocAsync((void**)&d3, sizeof(float) * B * NO, s))) return e;
+        if ((e = cudaMallocAsync((void**)&da, sizeof(float) * B * NH, s))) return e;
+        if ((e = cudaMallocAsync((void**)&d, sizeof(float) * B * NH, s))) return e;
+        return cudaMallocAsync((void**)&loss, sizeof(float), s);
+    }
+    void release(cudaStream_t s)
+    {
+        for (float* p : {xb, tb, z1, a1, z2, a2, z3, d3, da, d, loss})
+            if (p) cudaFreeAsync(p, s);
+    }
+};
+
+void gemm(const float* A, const float* B, float* C, int M, int N, int K, int ta, int tb, cudaStream_t s)
+{
+    dim3 grid((N + 63) / 64, (M + 63) / 64);
+    gemm_kernel<<<grid, 256, 0, s>>>(A, B, C, M, N, K, ta, tb);
+}
+
+// forward + backward of one batch already in w.xb / w.tb; gradient into net->G, loss added to *w.loss
+void fwd_bwd(skirt_mlp_s* net, Work& w, int B, cudaStream_t s)
+{
+    const float* P = net->P;
+    float* G = net->G;
+    gemm(w.xb, P + OFF_W1, w.z1, B, NH, NIN, 0, 1, s);
+    bias_silu_kernel<<<blocks_for((long long)B * NH, 256), 256, 0, s>>>(w.z1, w.a1, P + OFF_B1, B, NH);
+    gemm(w.a1, P + OFF_W2, w.z2, B, NH, NH, 0, 1, s);
+    bias_silu_kernel<<<blocks_for((long long)B * NH, 256), 256, 0, s>>>(w.z2, w.a2, P + OFF_B2, B, NH);
+    gemm(w.a2, P + OFF_W3, w.z3, B, NO, NH, 0, 1, s);
+    softmax_xent_kernel<<<(B * 32 + 255) / 256, 256, 0, s>>>(w.z3, P + OFF_B3, w.tb, w.d3, B, w.loss);
+    // layer 3
+    gemm(w.d3, w.a2, G + OFF_W3, NO, NH, B, 1, 0, s);
+    colsum_kernel<<<NO, 256, 0, s>>>(w.d3, G + OFF_B3, B, NO);
+    gemm(w.d3, P + OFF_W3, w.da, B, NH, NO, 0, 0, s);
+    silu_back_kernel<<<blocks_for((long long)B * NH, 256), 256, 0, s>>>(w.z2, w.da, w.d, (long long)B * NH);
+    // layer 2
+    gemm(w.d, w.a1, G + OFF_W2, NH, NH, B, 1, 0, s);
+    colsum_kernel<<<NH, 256, 0, s>>>(w.d, G + OFF_B2, B, NH);
+    gemm(w.d, P + OFF_W2, w.da, B, NH, NH, 0, 0, s);
+    silu_back_kernel<<<blocks_for((long long)B * NH, 256), 256, 0, s>>>(w.z1, w.da, w.d, (long long)B * NH);
+    // layer 1
+    gemm(w.d, w.xb, G + OFF_W1, NH, NIN, B, 1, 0, s);
+    colsum_kernel<<<NH, 256, 0, s>>>(w.d, G + OFF_B1, B, NH);
+}
+
+}  // namespace
+
+extern "C" int skirt_mlp_grad(skirt_mlp_t net, const float* x_std, const float* target, int n, float* grad,
+                              float* loss, void* stream)
+{
+    if (!net || !x_std || !target || n < 1) return set_error(SKIRT_ERR_INVALID_ARG, "net / x_std / target / n");
+    cudaStream_t s = (cudaStream_t)stream;
+    Work w;
+    MCK(w.alloc(n, s));
+    MCK(cudaMemcpyAsync(w.xb, x_std, sizeof(float) * n * NIN, cudaMemcpyDefault, s));
+    MCK(cudaMemcpyAsync(w.tb, target, sizeof(float) * n * NO, cudaMemcpyDefault, s));
+    MCK(cudaMemsetAsync(w.loss, 0, sizeof(float), s));
+    fwd_bwd(net, w, n, s);
+    MCK(cudaGetLastError());
+    if (grad) MCK(cudaMemcpyAsync(grad, net->G, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, s));
+    float l = 0.f;
+    MCK(cudaMemcpyAsync(&l, w.loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+    w.release(s);
+    MCK(cudaStreamSynchronize(s));
+    if (loss) *loss = l;
+    return SKIRT_OK;
+}
+
+extern "C" int skirt_mlp_train(skirt_mlp_t net, const float* features, const float* target, long long n,
+                               const skirt_mlp_train_opts* opts, float* loss_history, void* stream)
+{
+    if (!net || !features || !target || !opts) return set_error(SKIRT_ERR_INVALID_ARG, "net / data / opts is NULL");
+    const int B = opts->batch;
+    if (B < 32 || B > (1 << 16) || n < B) return set_error(SKIRT_ERR_INVALID_ARG, "batch must be in [32, 65536] and <= n");
+    if (opts->epochs < 1 || !(opts->lr > 0)) return set_error(SKIRT_ERR_INVALID_ARG, "epochs / lr invalid");
+    cudaStream_t s = (cudaStream_t)stream;
+    // standardisation and hull from the training features
+    double* d_st = nullptr;
+    MCK(cudaMallocAsync((void**)&d_st, sizeof(double) * 4 * NIN, s));
+    feature_stats_kernel<<<NIN, 256, 0, s>>>(features, n, d_st);
+    MCK(cudaGetLastError());
+    double st[4 * NIN];
+    MCK(cudaMemcpyAsync(st, d_st, sizeof st, cudaMemcpyDeviceToHost, s));
+    MCK(cudaStreamSynchronize(s));
+    cudaFreeAsync(d_st, s);
+    for (int k = 0; k < NIN; ++k) {
+        const double mean = st[4 * k] / (double)n;
+        const double var = st[4 * k + 1] / (double)n - mean * mean;
+        net->host_stats[k] = (float)mean;
+        net->host_stats[NIN + k] = (float)std::sqrt(var > 1e-12 ? var : 1e-12);
+        net->host_stats[2 * NIN + k] = (float)st[4 * k + 2];
+        net->host_stats[3 * NIN + k] = (float)st[4 * k + 3];
+    }
+    if (int r = upload_stats(net)) return r;
+    MCK(cudaMemsetAsync(net->Mo, 0, sizeof(float) * NPARAM, s));
+    MCK(cudaMemsetAsync(net->Vo, 0, sizeof(float) * NPARAM, s));
+    Work w;
+    MCK(w.alloc(B, s));
+    const long long steps = n / B;
+    const long long total_steps = steps * opts->epochs;
+    uint64_t rs = opts->seed ^ 0x5DEECE66Dull;
+    long long t = 0;
+    for (int ep = 0; ep < opts->epochs; ++ep) {
+        // affine permutation i -> (a i + b) mod n with a coprime to n
+        unsigned long long a = (splitmix64(rs) % (unsigned long long)n) | 1ull;
+        auto gcd = [](unsigned long long x, unsigned long long y) {
+            while (y) { unsigned long long r = x % y; x = y; y = r; }
+            return x;
+        };
+        while (gcd(a, (unsigned long long)n) != 1) a += 2;
+        const unsigned long long b = splitmix64(rs) % (unsigned long long)n;
+        MCK(cudaMemsetAsync(w.loss, 0, sizeof(float), s));
+        for (long long k = 0; k < steps; ++k, ++t) {
+            gather_kernel<<<blocks_for((long long)B * (NIN + NO), 256), 256, 0, s>>>(features, target, n, k * B, a, b,
+                                                                                    B, net->stats, w.xb, w.tb);
+            fwd_bwd(net, w, B, s);
+            const double frac = (double)t / (double)(total_steps > 1 ? total_steps - 1 : 1);
+            const float lr = (float)(opts->lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(M_PI * frac))));
+            const float c1 = 1.f - std::pow(opts->beta1, (float)(t + 1));
+            const float c2 = 1.f - std::pow(opts->beta2, (float)(t + 1));
+            adam_kernel<<<blocks_for(NPARAM, 256), 256, 0, s>>>(net->P, net->G, net->Mo, net->Vo, NPARAM, lr,
+                                                                opts->beta1, opts->beta2, opts->eps, c1, c2);
+        }
+        MCK(cudaGetLastError());
+        if (loss_history) {
+            float l = 0.f;
+            MCK(cudaMemcpyAsync(&l, w.loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+            MCK(cudaStreamSynchronize(s));
+            loss_history[ep] = l / (float)steps;
+        }
+    }
+    w.release(s);
+    if (int r = repack(net, s)) return r;
+    MCK(cudaStreamSynchronize(s));
+    return SKIRT_OK;
+}
+
+extern "C" int skirt_mlp_forward(skirt_mlp_t net, const float* features, const double* total, long long n,
+                                 double* emission, unsigned char* flags, void* stream)
+{
+    if (!net || !features || !total || !emission || n < 0) return set_error(SKIRT_ERR_INVALID_ARG, "mlp forward args");
+    if (n == 0) return SKIRT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int r = mlp_forward_internal(net, features, total, n, emission, flags, s);
+    if (r) return r;
+    MCK(cudaStreamSynchronize(s));
+    return SKIRT_OK;
+}

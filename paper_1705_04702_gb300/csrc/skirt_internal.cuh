@@ -181,7 +181,16 @@ struct skirt_grid_s {
     std::vector<unsigned char> gkey;
 };
 
+struct skirt_mlp_s;
+
 namespace skirt {
+// mlp.cu: tensor-core inference of the emission surrogate (stream-ordered, no sync)
+int mlp_forward_internal(skirt_mlp_s* net, const float* features, const double* total, long long n,
+                         double* emission, unsigned char* flags, cudaStream_t s);
+// emission.cu: exact FP64 emission of rows (all rows when rows == NULL)
+int launch_exact_emission(const double* absorbed, int n_in, const double* w_dev, const float* mass,
+                          const unsigned* rows, long long nrows, double* emission, float* temperature,
+                          cudaStream_t s);
 // dust_source.cu: per-wavelength cumulative distribution of emission[cell][lambda]
 // over the cells, normalised to 1, into grid->cdf.  INVALID_ARG when a
 // wavelength with packets has no (or non-finite / negative) emission.

@@ -272,3 +272,156 @@ def run_problem(prob, grid: Grid | None = None, precision=PREC_MIXED, schedule=S
     if own:
         grid.close()
     return out
+
+
+# ------------------------------------------------------------ dust emission
+EMIT_EXACT, EMIT_SURROGATE = 0, 1
+NBANDS, NEMIT, MLP_HIDDEN = 32, 100, 128
+MLP_NPARAM = 128 * 32 + 128 + 128 * 128 + 128 + 100 * 128 + 100
+
+
+class skirt_mlp_train_opts(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("seed", ctypes.c_uint64)]
+
+
+class skirt_emission_stats(ctypes.Structure):
+    _fields_ = [("n_cells", ctypes.c_ulonglong), ("n_fallback", ctypes.c_ulonglong),
+                ("ms_features", ctypes.c_float), ("ms_surrogate", ctypes.c_float), ("ms_exact", ctypes.c_float)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+def _bind_emission(L):
+    vp, i, ll, fp = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.POINTER(ctypes.c_float)
+    L.skirt_emission_grid.argtypes = [_dp, _dp]
+    L.skirt_dust_mass.argtypes = [vp, vp, vp]
+    L.skirt_band_features.argtypes = [vp, ll, i, _dp, vp, vp, vp, vp]
+    L.skirt_mlp_create.argtypes = [ctypes.POINTER(vp), ctypes.c_uint64]
+    L.skirt_mlp_destroy.argtypes = [vp]
+    L.skirt_mlp_set_params.argtypes = [vp, fp, fp, fp, fp, fp]
+    L.skirt_mlp_get_params.argtypes = [vp, fp, fp, fp, fp, fp]
+    L.skirt_mlp_train_opts_default.argtypes = [ctypes.POINTER(skirt_mlp_train_opts)]
+    L.skirt_mlp_train.argtypes = [vp, vp, vp, ll, ctypes.POINTER(skirt_mlp_train_opts), fp, vp]
+    L.skirt_mlp_grad.argtypes = [vp, vp, vp, i, fp, fp, vp]
+    L.skirt_mlp_forward.argtypes = [vp, vp, vp, ll, vp, vp, vp]
+    L.skirt_dust_emission.argtypes = [vp, ll, i, _dp, vp, i, vp, vp, vp, ctypes.POINTER(skirt_emission_stats), vp]
+    for name in ("skirt_emission_grid", "skirt_dust_mass", "skirt_band_features", "skirt_mlp_create",
+                 "skirt_mlp_destroy", "skirt_mlp_set_params", "skirt_mlp_get_params", "skirt_mlp_train_opts_default",
+                 "skirt_mlp_train", "skirt_mlp_grad", "skirt_mlp_forward", "skirt_dust_emission"):
+        getattr(L, name).restype = i
+
+
+_bind_emission(lib)
+
+
+def _st(stream):
+    return None if stream is None else ctypes.c_void_p(int(stream))
+
+
+def _fp(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float32).ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def skirt_emission_grid():
+    lam = np.zeros(NEMIT)
+    W = np.zeros(NEMIT)
+    _check(lib.skirt_emission_grid(lam.ctypes.data_as(_dp), W.ctypes.data_as(_dp)), "skirt_emission_grid")
+    return lam, W
+
+
+def skirt_dust_mass(grid, mass, stream=None):
+    _check(lib.skirt_dust_mass(grid, _ptr(mass), _st(stream)), "skirt_dust_mass")
+
+
+def skirt_band_features(absorbed, ncell, n_in, lambda_in, mass, features, total, stream=None):
+    lam = np.ascontiguousarray(lambda_in, dtype=np.float64)
+    _check(lib.skirt_band_features(_ptr(absorbed), int(ncell), int(n_in), lam.ctypes.data_as(_dp), _ptr(mass),
+                                   _ptr(features), _ptr(total), _st(stream)), "skirt_band_features")
+
+
+def skirt_dust_emission(absorbed, ncell, n_in, lambda_in, mass, mode, net, emission, temperature=None, stream=None):
+    lam = np.ascontiguousarray(lambda_in, dtype=np.float64)
+    st = skirt_emission_stats()
+    _check(lib.skirt_dust_emission(_ptr(absorbed), int(ncell), int(n_in), lam.ctypes.data_as(_dp), _ptr(mass),
+                                   int(mode), None if net is None else net.h, _ptr(emission), _ptr(temperature),
+                                   ctypes.byref(st), _st(stream)), "skirt_dust_emission")
+    return st.as_dict()
+
+
+class MLP:
+    """Owns a skirt_mlp_t (the emission surrogate network)."""
+
+    def __init__(self, seed=1):
+        self.h = ctypes.c_void_p()
+        _check(lib.skirt_mlp_create(ctypes.byref(self.h), int(seed)), "skirt_mlp_create")
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            lib.skirt_mlp_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params=None, x_mean=None, x_std=None, hull_lo=None, hull_hi=None):
+        keep = [None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+                for a in (params, x_mean, x_std, hull_lo, hull_hi)]
+        ptrs = [None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) for a in keep]
+        _check(lib.skirt_mlp_set_params(self.h, *ptrs), "skirt_mlp_set_params")
+
+    def get_params(self):
+        out = [np.zeros(MLP_NPARAM, np.float32)] + [np.zeros(NBANDS, np.float32) for _ in range(4)]
+        _check(lib.skirt_mlp_get_params(self.h, *[a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) for a in out]),
+               "skirt_mlp_get_params")
+        return out  # params, mean, std, lo, hi
+
+    def train(self, features, target, n, epochs=None, batch=None, lr=None, seed=None, stream=None):
+        o = skirt_mlp_train_opts()
+        _check(lib.skirt_mlp_train_opts_default(ctypes.byref(o)), "skirt_mlp_train_opts_default")
+        if epochs is not None:
+            o.epochs = int(epochs)
+        if batch is not None:
+            o.batch = int(batch)
+        if lr is not None:
+            o.lr = float(lr)
+        if seed is not None:
+            o.seed = int(seed)
+        hist = np.zeros(o.epochs, np.float32)
+        _check(lib.skirt_mlp_train(self.h, _ptr(features), _ptr(target), int(n), ctypes.byref(o),
+                                   hist.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _st(stream)), "skirt_mlp_train")
+        return hist
+
+    def grad(self, x_std, target, n, stream=None):
+        g = np.zeros(MLP_NPARAM, np.float32)
+        loss = ctypes.c_float()
+        _check(lib.skirt_mlp_grad(self.h, _ptr(x_std), _ptr(target), int(n),
+                                  g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(loss), _st(stream)),
+               "skirt_mlp_grad")
+        return g, loss.value
+
+    def forward(self, features, total, n, emission, flags=None, stream=None):
+        _check(lib.skirt_mlp_forward(self.h, _ptr(features), _ptr(total), int(n), _ptr(emission), _ptr(flags),
+                                     _st(stream)), "skirt_mlp_forward")
+
+
+def unpack_params(p):
+    """Packed FP32 parameter vector -> dict W1 b1 W2 b2 W3 b3 (float64)."""
+    p = np.asarray(p, dtype=np.float64)
+    o = 0
+    out = {}
+    for name, shape in (("W1", (128, 32)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)), ("W3", (100, 128)),
+                        ("b3", (100,))):
+        k = int(np.prod(shape))
+        out[name] = p[o:o + k].reshape(shape)
+        o += k
+    return out
+
+
+def pack_params(d):
+    return np.concatenate([np.asarray(d[k], dtype=np.float32).ravel() for k in ("W1", "b1", "W2", "b2", "W3", "b3")])

@@ -296,3 +296,25 @@ def beam_problem(grid: Grid, pos, direction, npackets=1, albedo=0.0, g=0.0,
         npk=np.array([npackets], dtype=np.uint64),
         instruments=list(instruments or []),
     )
+
+
+# ----------------------------------------------------------------------------
+# synthetic absorbed radiation fields (training and test inputs of the
+# dust-emission step)
+# ----------------------------------------------------------------------------
+def absorbed_spectra(n, lam, seed=1, median=1.0, sigma_dex=1.0):
+    """n absorbed spectra over the wavelengths ``lam`` [micron] and dust
+    masses: a power law lambda^alpha (alpha uniform in [-2, 0.5]) attenuated by
+    exp(-tau_V (lambda/0.55)^-1.2) (tau_V log-uniform in [1e-3, 1e2]), scaled so
+    that the absorbed power per unit mass is log-normal with the given median
+    and width in dex; masses log-uniform in [1e-7, 1e-4].  Returns
+    (absorbed [n, len(lam)] float64, mass [n] float32)."""
+    rng = np.random.default_rng(seed)
+    lam = np.asarray(lam, dtype=np.float64)
+    alpha = rng.uniform(-2.0, 0.5, n)
+    tau_v = 10 ** rng.uniform(-3.0, 2.0, n)
+    shape = lam[None, :] ** alpha[:, None] * np.exp(-tau_v[:, None] * (lam[None, :] / 0.55) ** -1.2)
+    shape /= shape.sum(axis=1, keepdims=True)
+    mass = (10 ** rng.uniform(-7.0, -4.0, n)).astype(np.float32)
+    per_mass = median * 10 ** (sigma_dex * rng.normal(size=n))
+    return shape * (per_mass * mass.astype(np.float64))[:, None], mass

@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -72,3 +73,13 @@ def test_no_device_is_reported_not_crashed(skirt):
     bb = (ctypes.c_double * 6)(-1, 1, -1, 1, -1, 1)
     dummy = (ctypes.c_float * 8)()
     assert skirt.lib.skirt_grid_create(ctypes.byref(h), 2, 2, 2, bb, dummy) == skirt.ERR_NO_DEVICE
+
+
+def test_emission_grid_matches_the_oracle(skirt):
+    """The library's output wavelength grid (host code) against the oracle's
+    independently written one."""
+    from oracle import emission as E
+    lam, W = skirt.skirt_emission_grid()
+    lam2, W2 = E.emission_grid()
+    np.testing.assert_allclose(lam, lam2, rtol=1e-14)
+    np.testing.assert_allclose(W, W2, rtol=1e-13)

@@ -1,0 +1,168 @@
+"""GPU parity of the dust-emission step and of its MLP surrogate (band
+compression, exact FP64 solver, training gradients, tensor-core inference,
+hull fallback) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import emission as E
+from paper_1705_04702_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1705_04702_gb300 import build
+    build.build()
+    from paper_1705_04702_gb300 import skirt
+    return skirt
+
+
+def _dev(a, dtype):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+@pytest.fixture(scope="module")
+def fields():
+    lam = np.geomspace(0.09, 10.0, 200)
+    a, m = W.absorbed_spectra(3000, lam, seed=5)
+    a[:3] = 0.0          # cells without absorbed power
+    m[3:6] = 0.0         # dust-free cells
+    return lam, a, m
+
+
+def test_band_features_match_oracle(S, fields):
+    import torch
+    lam, a, m = fields
+    n = a.shape[0]
+    feat = torch.zeros((n, 32), dtype=torch.float32, device="cuda")
+    tot = torch.zeros(n, dtype=torch.float64, device="cuda")
+    S.skirt_band_features(_dev(a, torch.float64), n, lam.size, lam, _dev(m, torch.float32), feat, tot)
+    B, x, total = E.band_features(a, lam, m.astype(np.float64))
+    np.testing.assert_allclose(tot.cpu().numpy(), total, rtol=1e-13, atol=0)
+    # FP32 log10 of the FP64 band power per unit mass: ~1e-7 relative inside log10
+    np.testing.assert_allclose(feat.cpu().numpy(), x, rtol=0, atol=2e-6)
+
+
+def test_exact_emission_matches_oracle(S, fields):
+    import torch
+    lam, a, m = fields
+    n = a.shape[0]
+    em = torch.zeros((n, 100), dtype=torch.float64, device="cuda")
+    T = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    st = S.skirt_dust_emission(_dev(a, torch.float64), n, lam.size, lam, _dev(m, torch.float32), S.EMIT_EXACT,
+                               None, em, T)
+    assert st["n_cells"] == n and st["n_fallback"] == 0
+    ref, Tref, P = E.exact_emission(a, lam, m.astype(np.float64))
+    g = em.cpu().numpy()
+    big = ref > 1e-9 * ref.sum(axis=1, keepdims=True)
+    np.testing.assert_allclose(g[big], ref[big], rtol=1e-9)
+    np.testing.assert_allclose(T.cpu().numpy(), Tref, rtol=1e-6)
+    # energy: every row sums to the cell's absorbed power
+    good = (m > 0) & (a.sum(axis=1) > 0)
+    np.testing.assert_allclose(g[good].sum(axis=1), a[good].sum(axis=1), rtol=1e-12)
+    assert np.all(g[~good] == 0)
+
+
+def _small_params(seed):
+    rng = np.random.default_rng(seed)
+    return {"W1": rng.normal(size=(128, 32)) * 0.25, "b1": rng.normal(size=128) * 0.1,
+            "W2": rng.normal(size=(128, 128)) * 0.09, "b2": rng.normal(size=128) * 0.1,
+            "W3": rng.normal(size=(100, 128)) * 0.09, "b3": rng.normal(size=100) * 0.1}
+
+
+def test_training_gradient_matches_oracle(S):
+    import torch
+    rng = np.random.default_rng(11)
+    P = _small_params(3)
+    net = S.MLP(seed=1)
+    net.set_params(S.pack_params(P))
+    P32 = S.unpack_params(S.pack_params(P))  # the FP32 values the device holds
+    n = 257  # ragged: not a multiple of the GEMM tiles
+    x = rng.normal(size=(n, 32)).astype(np.float32)
+    t = rng.random((n, 100))
+    t = (t / t.sum(axis=1, keepdims=True)).astype(np.float32)
+    g, loss = net.grad(_dev(x, torch.float32), _dev(t, torch.float32), n)
+    ref = E.mlp_grad(P32, x.astype(np.float64), t.astype(np.float64))
+    assert loss == pytest.approx(E.mlp_loss(P32, x.astype(np.float64), t.astype(np.float64)), rel=1e-5)
+    gd = S.unpack_params(g)
+    for k in ref:
+        scale = np.abs(ref[k]).max()
+        np.testing.assert_allclose(gd[k], ref[k], rtol=0, atol=2e-4 * scale, err_msg=k)
+    net.close()
+
+
+def test_tensor_core_inference_matches_oracle(S):
+    import torch
+    rng = np.random.default_rng(12)
+    P = _small_params(4)
+    Pb = S.unpack_params(S.pack_params(P))
+    Pb = {k: (E.bf16_round(v) if k.startswith("W") else v) for k, v in Pb.items()}
+    mean = rng.normal(size=32).astype(np.float32)
+    std = (0.5 + rng.random(32)).astype(np.float32)
+    lo = (mean - 2 * std).astype(np.float32)
+    hi = (mean + 2 * std).astype(np.float32)
+    net = S.MLP(seed=1)
+    net.set_params(S.pack_params(P), mean, std, lo, hi)
+    n = 1000 + 37  # several 64-row tiles and a ragged tail
+    x = (mean + std * rng.normal(size=(n, 32)) * 0.8).astype(np.float32)
+    x[5, 7] = hi[7] + 1.0  # outside the hull
+    x[9, 0] = lo[0] - 1.0
+    tot = 10 ** rng.uniform(-3, 3, n)
+    em = torch.zeros((n, 100), dtype=torch.float64, device="cuda")
+    flags = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    net.forward(_dev(x, torch.float32), _dev(tot, torch.float64), n, em, flags)
+    xs = (x.astype(np.float64) - mean) / std.astype(np.float64)
+    p, _ = E.mlp_forward(Pb, xs, act_bf16=True)
+    ref = p * tot[:, None]
+    g = em.cpu().numpy()
+    np.testing.assert_allclose(g.sum(axis=1), tot, rtol=1e-5)
+    rel = np.abs(g - ref) / ref
+    assert np.percentile(rel, 99) < 2e-3 and rel.max() < 3e-2
+    f = flags.cpu().numpy()
+    expect = np.any((x < lo) | (x > hi), axis=1)
+    assert np.array_equal(f.astype(bool), expect) and f[5] == 1 and f[9] == 1
+    net.close()
+
+
+def test_training_reaches_two_percent_and_fallback_is_exact(S):
+    """Train on exact solutions of synthetic fields; held-out emission within
+    2% (per-cell relative L2, median and 95th percentile); the surrogate mode
+    sends out-of-hull cells to the exact solver."""
+    import torch
+    lam = np.geomspace(0.09, 10.0, 200)
+    n_train, n_test = 60000, 4000
+    a, m = W.absorbed_spectra(n_train + n_test, lam, seed=21)
+    ad, md = _dev(a, torch.float64), _dev(m, torch.float32)
+    N = a.shape[0]
+    feat = torch.zeros((N, 32), dtype=torch.float32, device="cuda")
+    tot = torch.zeros(N, dtype=torch.float64, device="cuda")
+    S.skirt_band_features(ad, N, lam.size, lam, md, feat, tot)
+    ex = torch.zeros((N, 100), dtype=torch.float64, device="cuda")
+    S.skirt_dust_emission(ad, N, lam.size, lam, md, S.EMIT_EXACT, None, ex)
+    target = (ex / tot[:, None]).float()
+    net = S.MLP(seed=3)
+    hist = net.train(feat[:n_train].contiguous(), target[:n_train].contiguous(), n_train, epochs=40, batch=1024,
+                     lr=3e-3, seed=5)
+    assert hist[-1] < hist[0]
+    # held-out cells through the surrogate mode of skirt_dust_emission
+    em = torch.zeros((n_test, 100), dtype=torch.float64, device="cuda")
+    st = S.skirt_dust_emission(ad[n_train:].contiguous(), n_test, lam.size, lam, md[n_train:].contiguous(),
+                               S.EMIT_SURROGATE, net, em)
+    ref = ex[n_train:].cpu().numpy()
+    err = E.relative_l2(em.cpu().numpy(), ref)
+    assert np.median(err) < 0.02 and np.percentile(err, 95) < 0.05, (np.median(err), np.percentile(err, 95))
+    np.testing.assert_allclose(em.cpu().numpy().sum(axis=1), ref.sum(axis=1), rtol=1e-5)
+    # cells pushed outside the hull go to the exact solver and match it exactly
+    a2 = a[n_train:n_train + 50].copy() * 1e6
+    em2 = torch.zeros((50, 100), dtype=torch.float64, device="cuda")
+    st2 = S.skirt_dust_emission(_dev(a2, torch.float64), 50, lam.size, lam, md[n_train:n_train + 50].contiguous(),
+                                S.EMIT_SURROGATE, net, em2)
+    assert st2["n_fallback"] == 50
+    ref2, _, _ = E.exact_emission(a2, lam, m[n_train:n_train + 50].astype(np.float64))
+    np.testing.assert_allclose(em2.cpu().numpy(), ref2, rtol=1e-9, atol=1e-12 * ref2.max())
+    net.close()
