@@ -105,7 +105,8 @@ typedef struct {
     const double* kscale; /* kappa_ext(lambda) / kappa_ext(reference), finite, >= 0 */
     const double* albedo; /* scattering albedo in [0, 1] */
     const double* g;      /* Henyey-Greenstein asymmetry, |g| < 1 */
-    const double* lsrc;   /* luminosity emitted in this wavelength bin, >= 0 */
+    const double* lsrc;   /* luminosity emitted in this wavelength bin, >= 0; may be NULL for a
+                             dust-cell source: then the column sums of its emission table */
 } skirt_wavelengths;
 
 /* ----------------------------------------------------------- instruments */

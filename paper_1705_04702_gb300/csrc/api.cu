@@ -253,7 +253,9 @@ int validate(skirt_grid_t g, const skirt_source* src, const skirt_wavelengths* w
     if (cudaGetDevice(&dev) != cudaSuccess || dev != g->device)
         return fail(SKIRT_ERR_NO_DEVICE, "grid lives on device %d, current device is %d", g->device, dev);
     if (wl->n < 1 || wl->n > 65536) return fail(SKIRT_ERR_INVALID_ARG, "wavelength count %d out of range", wl->n);
-    if (!wl->kscale || !wl->albedo || !wl->g || !wl->lsrc) return fail(SKIRT_ERR_INVALID_ARG, "wavelength table is NULL");
+    if (!wl->kscale || !wl->albedo || !wl->g) return fail(SKIRT_ERR_INVALID_ARG, "wavelength table is NULL");
+    if (!wl->lsrc && src->kind != SKIRT_SRC_DUST)
+        return fail(SKIRT_ERR_INVALID_ARG, "lsrc may be NULL only for a dust-cell source");
     if (ninstr < 0 || ninstr > 16) return fail(SKIRT_ERR_INVALID_ARG, "ninstr must be in [0, 16]");
     if (ninstr > 0 && !ins) return fail(SKIRT_ERR_INVALID_ARG, "instruments are NULL");
     P.NL = wl->n;
@@ -262,7 +264,8 @@ int validate(skirt_grid_t g, const skirt_source* src, const skirt_wavelengths* w
         if (!std::isfinite(wl->kscale[j]) || wl->kscale[j] < 0) return fail(SKIRT_ERR_INVALID_ARG, "kscale[%d] invalid", j);
         if (!(wl->albedo[j] >= 0 && wl->albedo[j] <= 1)) return fail(SKIRT_ERR_INVALID_ARG, "albedo[%d] not in [0,1]", j);
         if (!(std::fabs(wl->g[j]) < 1)) return fail(SKIRT_ERR_INVALID_ARG, "|g[%d]| must be < 1", j);
-        if (!std::isfinite(wl->lsrc[j]) || wl->lsrc[j] < 0) return fail(SKIRT_ERR_INVALID_ARG, "lsrc[%d] invalid", j);
+        if (wl->lsrc && (!std::isfinite(wl->lsrc[j]) || wl->lsrc[j] < 0))
+            return fail(SKIRT_ERR_INVALID_ARG, "lsrc[%d] invalid", j);
         if (npk[j] >= (1ull << 32)) return fail(SKIRT_ERR_INVALID_ARG, "npackets[%d] must be < 2^32", j);
     }
     P.offsets.assign(P.NL + 1, 0);
@@ -337,6 +340,17 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
     const int NL = P.NL;
     const Layout& L = P.lay;
 
+    // ---- dust source: per-wavelength cumulative distribution over the cells;
+    // its column totals are the source luminosities when lsrc is NULL
+    const double* d_cdf = nullptr;
+    std::vector<double> dust_totals;
+    if (src->kind == SKIRT_SRC_DUST) {
+        int r = build_dust_cdf(g, src->emission, NL, npk, s, &dust_totals);
+        if (r) return r;
+        d_cdf = (const double*)g->cdf.p;
+    }
+    const double* lsrc = wl->lsrc ? wl->lsrc : dust_totals.data();
+
     // ---- host staging: parameter tables and read-back area
     const size_t rb_ledger = sizeof(double) * 4 * NL, rb_counters = sizeof(unsigned long long) * 4;
     const size_t pinned_bytes = L.total + rb_ledger + rb_counters + 64;
@@ -356,7 +370,7 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
         h_ks[j] = wl->kscale[j];
         h_al[j] = wl->albedo[j];
         h_g[j] = wl->g[j];
-        h_L0[j] = npk[j] ? wl->lsrc[j] / (double)npk[j] : 0.0;
+        h_L0[j] = npk[j] ? lsrc[j] / (double)npk[j] : 0.0;
         h_ksf[j] = (float)h_ks[j];
         h_alf[j] = (float)h_al[j];
         h_gf[j] = (float)h_g[j];
@@ -401,13 +415,6 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
         if (peel && !sed_dev) CK(cudaMemcpyAsync(d_sed, sed, sed_bytes, cudaMemcpyHostToDevice, s));
     }
 
-    // ---- dust source: per-wavelength cumulative distribution over the cells
-    const double* d_cdf = nullptr;
-    if (src->kind == SKIRT_SRC_DUST) {
-        int r = build_dust_cdf(g, src->emission, NL, npk, s);
-        if (r) return r;
-        d_cdf = (const double*)g->cdf.p;
-    }
 
     // ---- kernel arguments
     TraceArgs A;

@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(SCAN_T) tile_scan_kernel(double* __restrict__ 
 
 }  // namespace
 
-int build_dust_cdf(skirt_grid_s* g, const double* emission, int nl, const uint64_t* npk, cudaStream_t s)
+int build_dust_cdf(skirt_grid_s* g, const double* emission, int nl, const uint64_t* npk, cudaStream_t s,
+                   std::vector<double>* totals_out)
 {
     const long long ncell = g->ncell;
     const int ntiles = (int)((ncell + TILE - 1) / TILE);
@@ -177,6 +178,7 @@ int build_dust_cdf(skirt_grid_s* g, const double* emission, int nl, const uint64
     for (int j = 0; j < nl; ++j)
         if (npk[j] > 0 && !(h[j] > 0.0 && isfinite(h[j])))
             return set_error(SKIRT_ERR_INVALID_ARG, "dust emission at wavelength %d is zero but has packets", j);
+    if (totals_out) totals_out->assign(h.begin(), h.begin() + nl);
     return SKIRT_OK;
 }
 

@@ -192,7 +192,9 @@ int launch_exact_emission(const double* absorbed, int n_in, const double* w_dev,
                           const unsigned* rows, long long nrows, double* emission, float* temperature,
                           cudaStream_t s);
 // dust_source.cu: per-wavelength cumulative distribution of emission[cell][lambda]
-// over the cells, normalised to 1, into grid->cdf.  INVALID_ARG when a
-// wavelength with packets has no (or non-finite / negative) emission.
-int build_dust_cdf(skirt_grid_s* g, const double* emission, int nlambda, const uint64_t* npk, cudaStream_t s);
+// over the cells, normalised to 1, into grid->cdf; the per-wavelength totals
+// into *totals_out (may be NULL).  INVALID_ARG when a wavelength with packets
+// has no (or non-finite / negative) emission.
+int build_dust_cdf(skirt_grid_s* g, const double* emission, int nlambda, const uint64_t* npk, cudaStream_t s,
+                   std::vector<double>* totals_out);
 }  // namespace skirt

@@ -182,9 +182,10 @@ class Tables:
         self.kscale = np.ascontiguousarray(wl.kscale, dtype=np.float64)
         self.albedo = np.ascontiguousarray(wl.albedo, dtype=np.float64)
         self.g = np.ascontiguousarray(wl.g, dtype=np.float64)
-        self.lsrc = np.ascontiguousarray(wl.lsrc, dtype=np.float64)
+        self.lsrc = None if wl.lsrc is None else np.ascontiguousarray(wl.lsrc, dtype=np.float64)
         self.c = skirt_wavelengths(wl.n, self.kscale.ctypes.data_as(_dp), self.albedo.ctypes.data_as(_dp),
-                                   self.g.ctypes.data_as(_dp), self.lsrc.ctypes.data_as(_dp))
+                                   self.g.ctypes.data_as(_dp),
+                                   None if self.lsrc is None else self.lsrc.ctypes.data_as(_dp))
 
 
 def make_source(s, emission=None) -> skirt_source:

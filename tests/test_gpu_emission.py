@@ -44,8 +44,8 @@ def test_band_features_match_oracle(S, fields):
     S.skirt_band_features(_dev(a, torch.float64), n, lam.size, lam, _dev(m, torch.float32), feat, tot)
     B, x, total = E.band_features(a, lam, m.astype(np.float64))
     np.testing.assert_allclose(tot.cpu().numpy(), total, rtol=1e-13, atol=0)
-    # FP32 log10 of the FP64 band power per unit mass: ~1e-7 relative inside log10
-    np.testing.assert_allclose(feat.cpu().numpy(), x, rtol=0, atol=2e-6)
+    # FP32 log10 of the FP64 band power per unit mass, stored as FP32: a few ulp
+    np.testing.assert_allclose(feat.cpu().numpy(), x, rtol=3e-7, atol=1e-6)
 
 
 def test_exact_emission_matches_oracle(S, fields):
@@ -157,8 +157,9 @@ def test_training_reaches_two_percent_and_fallback_is_exact(S):
     err = E.relative_l2(em.cpu().numpy(), ref)
     assert np.median(err) < 0.02 and np.percentile(err, 95) < 0.05, (np.median(err), np.percentile(err, 95))
     np.testing.assert_allclose(em.cpu().numpy().sum(axis=1), ref.sum(axis=1), rtol=1e-5)
-    # cells pushed outside the hull go to the exact solver and match it exactly
-    a2 = a[n_train:n_train + 50].copy() * 1e6
+    # cells pushed outside the hull (12 dex above every training cell's absorbed
+    # power per unit mass) go to the exact solver and match it exactly
+    a2 = a[n_train:n_train + 50].copy() * 1e12
     em2 = torch.zeros((50, 100), dtype=torch.float64, device="cuda")
     st2 = S.skirt_dust_emission(_dev(a2, torch.float64), 50, lam.size, lam, md[n_train:n_train + 50].contiguous(),
                                 S.EMIT_SURROGATE, net, em2)

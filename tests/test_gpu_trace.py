@@ -200,3 +200,34 @@ def test_invalid_arguments(S):
     g2.kr[0, 0, 0] = np.nan
     with pytest.raises(S.SkirtError):
         S.Grid(g2)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_dust_cell_source(S, oracle_lib, precision):
+    """Dust emission phase source: cells drawn from the per-wavelength CDF of
+    an emission table (built here with numpy, independently of the library's
+    scan), a uniform point inside the cell, isotropic direction; the source
+    luminosity of each wavelength is the table's column sum (lsrc = NULL)."""
+    import dataclasses
+    import torch
+    grid = W.sphere_grid(16, kr_in=2.0)
+    rng = np.random.default_rng(4)
+    nl = 3
+    em = rng.random((grid.ncell, nl)) ** 4 * (grid.kr.ravel()[:, None] > 0)
+    em[:, 1] *= 1e-3
+    totals = em.sum(axis=0)
+    cdf = np.cumsum(em, axis=0) / totals
+    cdf[-1] = 1.0
+    wl = W.powerlaw_wavelengths(nl, 1.0, 100.0, alb_short=0.3, alb_long=0.0)
+    prob = W.Problem("dust", grid, W.Source(W.SRC_DUST), wl, np.array([3000, 2000, 0], np.uint64),
+                     [W.Instrument(50.0, 30.0, 10.0, 2.0, 16)], seed=9)
+    prob.phase = 1
+    r = oracle_lib.trace(dataclasses.replace(prob, wl=dataclasses.replace(wl, lsrc=totals)), nrec=3000,
+                         cell_cdf=np.ascontiguousarray(cdf.T))
+    g = S.run_problem(dataclasses.replace(prob, wl=dataclasses.replace(wl, lsrc=None)), precision=precision,
+                      nrec=3000, emission=torch.as_tensor(em, device="cuda"))
+    rel = REL_FP64 if precision == 0 else REL_MIXED_PACKET
+    compare_records(_np(g["records"]), r["records"], prob.with_packets(prob.npk), rel, 0.999, same_n_min=0.999)
+    np.testing.assert_allclose(g["ledger_per_lambda"][:, 0], [totals[0], totals[1], 0.0], rtol=1e-6)
+    compare_tally(_np(g["absorbed"]), r["absorbed"], rel if precision == 0 else REL_MIXED_TALLY,
+                  significant=1e-6 if precision == 0 else MIXED_CELL_SIGNIFICANT)
