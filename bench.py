@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--autotune", action="store_true")
-    ap.add_argument("--workload", default="disk", choices=["disk", "disk40", "torus"],
+    ap.add_argument("--workload", default="disk", choices=["disk", "disk40", "torus", "learned"],
                     help="disk: 1 wavelength, --packets packets (default); disk40: 40 wavelengths, "
                          "--packets per wavelength; torus: clumpy torus, 200 wavelengths, uneven counts "
                          "(--packets scales them, 1e8 = the full 7.5e8-packet run)")
@@ -181,11 +181,31 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ learned
+def run_learned_report(args):
+    """The learned form on the clumpy torus (256^3, 200 wavelengths, then a
+    1e8-packet re-emission trace): stage times, surrogate error and
+    speedups, as one JSON line (not the headline metric)."""
+    import torch
+    from paper_1705_04702_gb300 import build
+    build.build()
+    from paper_1705_04702_gb300.learned import run_learned
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rep = run_learned(n=args.grid, nlambda=200, packet_scale=args.packets / 1e8, n_train=1_000_000,
+                      n_test=100_000, epochs=20, reemit_per_lambda=1_000_000)
+    rep = {k: v for k, v in rep.items() if not k.startswith("_")}
+    print(json.dumps({"report": "learned form", "workload": f"clumpy torus {args.grid}^3, 200 wavelengths",
+                      **rep}), flush=True)
+
+
 # ----------------------------------------------------------------------- ours
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "learned":
+        run_learned_report(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

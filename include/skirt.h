@@ -265,11 +265,12 @@ typedef struct {
 int skirt_mlp_train_opts_default(skirt_mlp_train_opts* opts);
 
 /* Trains on n samples: features (device float[n][32], raw band features)
- * and target (device float[n][100], emission shapes summing to 1) with the
- * cross-entropy loss -sum_l t_l log p_l.  Sets the standardisation and the
- * hull from the training features.  loss_history: host float[epochs] (mean
- * loss per epoch) or NULL. */
-int skirt_mlp_train(skirt_mlp_t net, const float* features, const float* target, long long n,
+ * and emission (device double[n][100], e.g. the exact solver's output; every
+ * row is normalised to sum 1 on the device and used as the target shape t)
+ * with the cross-entropy loss -sum_l t_l log p_l.  Sets the standardisation
+ * and the hull from the training features.  loss_history: host
+ * float[epochs] (mean loss per epoch) or NULL. */
+int skirt_mlp_train(skirt_mlp_t net, const float* features, const double* emission, long long n,
                     const skirt_mlp_train_opts* opts, float* loss_history, void* stream);
 
 /* One batch of the training arithmetic (FP32): loss and gradient of the

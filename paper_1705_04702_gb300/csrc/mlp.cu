@@ -365,6 +365,19 @@ __global__ void gather_kernel(const float* __restrict__ feat, const float* __res
     }
 }
 
+// out[r][c] = in[r][c] / sum_c in[r][c] in FP32 (one warp per row; zero rows stay zero)
+__global__ void normalize_rows_kernel(const double* __restrict__ in, float* __restrict__ out, long long rows)
+{
+    const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    double s = 0.0;
+    for (int c = lane; c < NO; c += 32) s += in[r * NO + c];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const double inv = s > 0.0 ? 1.0 / s : 0.0;
+    for (int c = lane; c < NO; c += 32) out[r * NO + c] = (float)(in[r * NO + c] * inv);
+}
+
 // per-feature sums over n samples: sum, sum of squares, min, max (one block per feature)
 __global__ void feature_stats_kernel(const float* feat, long long n, double* out)
 {
@@ -686,14 +699,19 @@ extern "C" int skirt_mlp_grad(skirt_mlp_t net, const float* x_std, const float* 
     return SKIRT_OK;
 }
 
-extern "C" int skirt_mlp_train(skirt_mlp_t net, const float* features, const float* target, long long n,
+extern "C" int skirt_mlp_train(skirt_mlp_t net, const float* features, const double* emission, long long n,
                                const skirt_mlp_train_opts* opts, float* loss_history, void* stream)
 {
-    if (!net || !features || !target || !opts) return set_error(SKIRT_ERR_INVALID_ARG, "net / data / opts is NULL");
+    if (!net || !features || !emission || !opts) return set_error(SKIRT_ERR_INVALID_ARG, "net / data / opts is NULL");
     const int B = opts->batch;
     if (B < 32 || B > (1 << 16) || n < B) return set_error(SKIRT_ERR_INVALID_ARG, "batch must be in [32, 65536] and <= n");
     if (opts->epochs < 1 || !(opts->lr > 0)) return set_error(SKIRT_ERR_INVALID_ARG, "epochs / lr invalid");
     cudaStream_t s = (cudaStream_t)stream;
+    // target shapes: every emission row normalised to sum 1
+    float* target = nullptr;
+    MCK(cudaMallocAsync((void**)&target, sizeof(float) * NO * (size_t)n, s));
+    normalize_rows_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(emission, target, n);
+    MCK(cudaGetLastError());
     // standardisation and hull from the training features
     double* d_st = nullptr;
     MCK(cudaMallocAsync((void**)&d_st, sizeof(double) * 4 * NIN, s));
@@ -750,6 +768,7 @@ extern "C" int skirt_mlp_train(skirt_mlp_t net, const float* features, const flo
         }
     }
     w.release(s);
+    cudaFreeAsync(target, s);
     if (int r = repack(net, s)) return r;
     MCK(cudaStreamSynchronize(s));
     return SKIRT_OK;

@@ -382,7 +382,10 @@ class MLP:
                "skirt_mlp_get_params")
         return out  # params, mean, std, lo, hi
 
-    def train(self, features, target, n, epochs=None, batch=None, lr=None, seed=None, stream=None):
+    def train(self, features, emission, n, epochs=None, batch=None, lr=None, seed=None, stream=None):
+        """features: device float [n, 32]; emission: device double [n, 100]
+        (target rows, normalised on the device)."""
+        target = emission
         o = skirt_mlp_train_opts()
         _check(lib.skirt_mlp_train_opts_default(ctypes.byref(o)), "skirt_mlp_train_opts_default")
         if epochs is not None:
