@@ -161,18 +161,25 @@ def band_index(lam_in, nbands=NBANDS):
     return np.clip(b, 0, nbands - 1)
 
 
+BAND_FLOOR_REL = 1e-6
+
+
 def band_features(absorbed, lam_in, mass, nbands=NBANDS):
-    """Band sums B [n, nbands], features log10(max(B / M, floor)) and the
-    total absorbed power [n]."""
+    """Band sums B [n, nbands], features and the total absorbed power T [n].
+    Feature b is log10(max(B_b, 1e-6 T / nbands) / M): a band without
+    absorbed power sits 6 dex (per band) below the cell's total instead of at
+    an absolute floor; cells without dust or absorbed power get log10(1e-30)."""
     absorbed = np.asarray(absorbed, dtype=np.float64)
     idx = band_index(lam_in, nbands)
     B = np.zeros((absorbed.shape[0], nbands))
     for j, b in enumerate(idx):
         B[:, b] += absorbed[:, j]
+    T = B.sum(axis=1)
     mass = np.asarray(mass, dtype=np.float64)
-    with np.errstate(divide="ignore", invalid="ignore"):
-        per_mass = np.where(mass[:, None] > 0, B / mass[:, None], 0.0)
-    x = np.log10(np.maximum(per_mass, FEATURE_FLOOR))
+    ok = (mass > 0) & (T > 0)
+    x = np.full(B.shape, math.log10(FEATURE_FLOOR))
+    floor = BAND_FLOOR_REL * T[ok, None] / nbands
+    x[ok] = np.log10(np.maximum(np.maximum(B[ok], floor) / mass[ok, None], FEATURE_FLOOR))
     return B, x, absorbed.sum(axis=1)
 
 

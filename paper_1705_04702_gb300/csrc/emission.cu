@@ -104,12 +104,20 @@ __global__ void band_features_kernel(const double* __restrict__ A, long long nce
          m += (long long)gridDim.x * blockDim.x) {
         const double* row = A + (size_t)m * n_in;
         const double M = (double)mass[m];
-        double tot = 0.0;
+        double B[NB], tot = 0.0;
+#pragma unroll
         for (int b = 0; b < NB; ++b) {
             double s = 0.0;
             for (int j = s_start[b]; j < s_start[b + 1]; ++j) s += row[j];
+            B[b] = s;
             tot += s;
-            const double pm = M > 0.0 ? s / M : 0.0;
+        }
+        // an empty band sits 6 dex (per band) below the cell's total power
+        const bool ok = M > 0.0 && tot > 0.0;
+        const double floor_b = 1e-6 * tot / NB;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const double pm = ok ? fmax(B[b], floor_b) / M : 0.0;
             features[(size_t)m * NB + b] = log10f(fmaxf((float)fmax(pm, 1e-30), 1e-30f));
         }
         total[m] = tot;

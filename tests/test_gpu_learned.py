@@ -13,7 +13,7 @@ def test_learned_pipeline_small():
     from paper_1705_04702_gb300 import build
     build.build()
     from paper_1705_04702_gb300.learned import run_learned
-    rep = run_learned(n=40, nlambda=40, packet_scale=2e-3, n_train=16000, n_test=3000, epochs=30, batch=1024,
+    rep = run_learned(n=40, nlambda=40, packet_scale=2e-3, n_train=16000, n_test=3000, epochs=150, batch=512,
                       lr=3e-3, reemit_per_lambda=2000)
     assert rep["loss_first_last"][1] < rep["loss_first_last"][0]
     # held-out cells of the traced torus: median within 2% of the exact solver
