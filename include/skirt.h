@@ -282,7 +282,8 @@ int skirt_mlp_grad(skirt_mlp_t net, const float* x_std, const float* target, int
 
 /* Tensor-core inference: emission (device double[n][100]) = softmax(MLP(
  * (features - mean) / std)) * total (device double[n]).  If flags is not
- * NULL (device unsigned char[n]) it receives 1 for rows outside the hull. */
+ * NULL (device unsigned char[n]) it receives 1 for rows with total > 0 whose
+ * features fall outside the hull. */
 int skirt_mlp_forward(skirt_mlp_t net, const float* features, const double* total, long long n,
                       double* emission, unsigned char* flags, void* stream);
 

@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(32 * INF_WARPS) mlp_infer_kernel(
                     const float v = xs[lane * NIN + k];
                     out |= !(v >= hlo[k] && v <= hhi[k]);
                 }
-                flags[r] = out ? 1 : 0;
+                // a cell without absorbed power emits nothing: no fallback needed
+                flags[r] = (out && total[r] > 0.0) ? 1 : 0;
             }
         }
         uint32_t a1[2][4];
