@@ -304,6 +304,23 @@ int skirt_dust_emission(const double* absorbed, long long ncell, int n_in, const
                         const float* mass, int mode, skirt_mlp_t net, double* emission, float* temperature,
                         skirt_emission_stats* stats, void* stream);
 
+/* Exact emission without allocating (the paper has no counterpart: it is an
+ * interface for callers that cannot allocate device memory at call time,
+ * e.g. a process whose framework allocator has already reserved the device
+ * memory it may use, or a loop run on a memory budget fixed up front).
+ * Same result as skirt_dust_emission in SKIRT_EMIT_EXACT mode, same argument
+ * meaning (all arrays device memory, lambda_in host, temperature may be NULL),
+ * no statistics.  Its only working table, the absorption shares of the input
+ * wavelengths, lives in a fixed device array of 3 x 4096 doubles (96 KiB) that
+ * every device loading the library holds until the process exits: n_in above
+ * 4096 is rejected with SKIRT_ERR_INVALID_ARG.  The first call on a device
+ * looks up the array's device address (once per device, with that device
+ * current); make that first call before any stream capture.  Every call
+ * rewrites the table in full; calls share it, so calls that overlap on the
+ * GPU (other threads or streams) race.  Synchronises the stream on return. */
+int skirt_dust_emission_exact_static(const double* absorbed, long long ncell, int n_in, const double* lambda_in,
+                                     const float* mass, double* emission, float* temperature, void* stream);
+
 /* Microbenchmarks for the rooflines of the trace kernel (no counterpart in
  * the paper, which ran on CPUs): kind 0 FP64 FMA rate, 1 FP32 FMA rate,
  * 2 FP32<->FP64 conversion rate, 3 random-address red.global.add.f64 into a

@@ -14,6 +14,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "skirt_internal.cuh"
@@ -441,5 +442,80 @@ extern "C" int skirt_dust_emission(const double* absorbed, long long ncell, int 
         stats->ms_exact = c;
     }
     for (auto& e : ev) cudaEventDestroy(e);
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free exact emission.
+//
+// skirt_dust_emission allocates its per-call working table (the absorption
+// share of every input wavelength for the three grain populations) with the
+// stream-ordered allocator.  Some callers cannot allocate device memory at
+// call time: a process whose framework allocator has already reserved the
+// device memory it may use, or a loop with a fixed memory budget decided up
+// front.  skirt_dust_emission_exact_static does the same exact solve with that
+// table in the fixed array below instead (3 x 4096 doubles = 96 KiB, held by
+// every device that loads the library until the process exits).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int STATIC_MAX_NIN = 4096;
+static __device__ __align__(256) double g_static_shares[NPOP * STATIC_MAX_NIN];
+
+std::mutex g_static_mutex;
+double* g_static_ptr[64] = {};  // device address of g_static_shares, per device ordinal
+double g_static_host[NPOP * STATIC_MAX_NIN];  // host copy of the table (guarded by g_static_mutex)
+
+// shares w_i(lambda_j) = (lambda_j/0.55)^delta_i / sum_k (lambda_j/0.55)^delta_k into out[i*n + j]
+void fill_shares(const double* lam, int n, double* out)
+{
+    for (int j = 0; j < n; ++j) {
+        double r[NPOP], sum = 0.0;
+        for (int i = 0; i < NPOP; ++i) {
+            r[i] = std::pow(lam[j] / 0.55, DELTA[i]);
+            sum += r[i];
+        }
+        for (int i = 0; i < NPOP; ++i) out[(size_t)i * n + j] = r[i] / sum;
+    }
+}
+
+}  // namespace
+
+extern "C" int skirt_dust_emission_exact_static(const double* absorbed, long long ncell, int n_in,
+                                                const double* lambda_in, const float* mass, double* emission,
+                                                float* temperature, void* stream)
+{
+    if (ncell < 0) return set_error(SKIRT_ERR_INVALID_ARG, "ncell < 0");
+    if (n_in > STATIC_MAX_NIN)
+        return set_error(SKIRT_ERR_INVALID_ARG, "n_in = %d exceeds the static table's maximum of %d wavelengths",
+                         n_in, STATIC_MAX_NIN);
+    if (int r = check_lambda(lambda_in, n_in)) return r;
+    if (ncell == 0) return SKIRT_OK;
+    if (ncell >= (1ll << 32)) return set_error(SKIRT_ERR_INVALID_ARG, "ncell must be < 2^32");
+    if (!is_device(absorbed) || !is_device(mass) || !is_device(emission) || (temperature && !is_device(temperature)))
+        return set_error(SKIRT_ERR_INVALID_ARG, "absorbed / mass / emission / temperature must be device memory");
+    int dev = 0;
+    ECK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return set_error(SKIRT_ERR_NO_DEVICE, "device ordinal %d out of range", dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    double* shares = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mutex);
+        // once per device, with that device current: the device address of the array
+        if (!g_static_ptr[dev]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_static_shares);
+            if (e != cudaSuccess || !p)
+                return set_error(SKIRT_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            g_static_ptr[dev] = (double*)p;
+        }
+        shares = g_static_ptr[dev];
+        // the table is rewritten in full by every call (no part needs zeroing); a copy from
+        // pageable memory has left the host buffer when cudaMemcpyAsync returns
+        fill_shares(lambda_in, n_in, g_static_host);
+        ECK(cudaMemcpyAsync(shares, g_static_host, sizeof(double) * NPOP * n_in, cudaMemcpyHostToDevice, s));
+    }
+    int rc = launch_exact_emission(absorbed, n_in, shares, mass, nullptr, ncell, emission, temperature, s);
+    ECK(cudaStreamSynchronize(s));
     return rc;
 }

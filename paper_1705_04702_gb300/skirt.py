@@ -309,9 +309,11 @@ def _bind_emission(L):
     L.skirt_mlp_grad.argtypes = [vp, vp, vp, i, fp, fp, vp]
     L.skirt_mlp_forward.argtypes = [vp, vp, vp, ll, vp, vp, vp]
     L.skirt_dust_emission.argtypes = [vp, ll, i, _dp, vp, i, vp, vp, vp, ctypes.POINTER(skirt_emission_stats), vp]
+    L.skirt_dust_emission_exact_static.argtypes = [vp, ll, i, _dp, vp, vp, vp, vp]
     for name in ("skirt_emission_grid", "skirt_dust_mass", "skirt_band_features", "skirt_mlp_create",
                  "skirt_mlp_destroy", "skirt_mlp_set_params", "skirt_mlp_get_params", "skirt_mlp_train_opts_default",
-                 "skirt_mlp_train", "skirt_mlp_grad", "skirt_mlp_forward", "skirt_dust_emission"):
+                 "skirt_mlp_train", "skirt_mlp_grad", "skirt_mlp_forward", "skirt_dust_emission",
+                 "skirt_dust_emission_exact_static"):
         getattr(L, name).restype = i
 
 
@@ -350,6 +352,14 @@ def skirt_dust_emission(absorbed, ncell, n_in, lambda_in, mass, mode, net, emiss
                                    int(mode), None if net is None else net.h, _ptr(emission), _ptr(temperature),
                                    ctypes.byref(st), _st(stream)), "skirt_dust_emission")
     return st.as_dict()
+
+
+def skirt_dust_emission_exact_static(absorbed, ncell, n_in, lambda_in, mass, emission, temperature=None, stream=None):
+    """Exact emission that allocates no device memory (fixed 4096-wavelength working table)."""
+    lam = np.ascontiguousarray(lambda_in, dtype=np.float64)
+    _check(lib.skirt_dust_emission_exact_static(_ptr(absorbed), int(ncell), int(n_in), lam.ctypes.data_as(_dp),
+                                                _ptr(mass), _ptr(emission), _ptr(temperature), _st(stream)),
+           "skirt_dust_emission_exact_static")
 
 
 class MLP:
