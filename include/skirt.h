@@ -150,7 +150,7 @@ typedef struct {
                           and replayed by later calls with identical arguments */
     int step_min;      /* mixed form: a warp keeps stepping cells while at least step_min of
                           its lanes are inside a traversal, then handles the events of the
-                          idle lanes together (1..32; 0 = default 16) */
+                          idle lanes together (1..32; 0 = default 20) */
     uint32_t phase;    /* random-stream phase: 0 stellar, 1 dust re-emission (< 256) */
     int nrec;          /* >= 0: per-packet records for packet indices < nrec */
     double* records;   /* device-or-host double[n][nrec][8]: scatterings, escaped, absorbed,

@@ -473,7 +473,7 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
     A.phase = opts->phase;
     A.queue = (unsigned long long*)(dp + L.queue);
     A.chunk = opts->chunk > 0 ? opts->chunk : 4;
-    A.step_min = opts->step_min > 0 ? opts->step_min : 16;
+    A.step_min = opts->step_min > 0 ? opts->step_min : 20;
 
     const int block = opts->block > 0 ? opts->block : 256;
     int bps = opts->blocks_per_sm;
@@ -628,9 +628,9 @@ extern "C" int skirt_autotune(skirt_grid_t g, const skirt_source* src, const ski
     const bool mixed = o.precision == SKIRT_PREC_MIXED;
     const int blocks[4] = {64, 128, 256, mixed ? 256 : 512};
     const int chunks[3] = {1, 4, 16};
-    const int step_mins[3] = {8, 16, 24};
+    const int step_mins[3] = {16, 20, 24};
     float best = 1e30f;
-    int bb = 256, bc = 4, bbps = 0, bsm = 16;
+    int bb = 256, bc = 4, bbps = 0, bsm = 20;
     for (int bi = 0; bi < 4; ++bi) {
         if (bi > 0 && blocks[bi] == blocks[bi - 1]) continue;
         int maxbps = 0;

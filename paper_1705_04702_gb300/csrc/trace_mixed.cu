@@ -43,7 +43,7 @@ namespace skirt {
 namespace {
 
 constexpr int MAXB = 256;       // threads per block of the mixed kernel (upper bound)
-constexpr int ROUND = 4;        // cell crossings per stepping round between warp votes
+constexpr int ROUND = 8;        // cell crossings per stepping round between warp votes
 constexpr float TAU_CUT = 50.f; // optical depth after which a deposit / peel-off traversal stops
 
 // FP32 -> FP64 by IEEE-754 field manipulation on the integer pipe: exact for
@@ -78,14 +78,16 @@ __device__ __forceinline__ float exp_neg(float x)
     return y;
 }
 
-// 1 - e^{-x} for x >= 0, accurate in relative terms: the alternating Taylor
-// series x - x^2/2! + ... + x^7/7! (Horner form) below 1/4, where the first
+// 1 - e^{-x} for x >= 0, accurate in relative terms: below 1/4 the Taylor
+// series x (1 - x g(x)) with g(x) = 1/2! - x/3! + x^2/4! - ... - x^5/7!
+// (Horner form with constant coefficients: six multiply-adds), whose first
 // omitted term is below 4e-10 of the result; 1 - e^{-x} above, where no
 // cancellation occurs.  Both branches are evaluated and selected.
 __device__ __forceinline__ float one_minus_exp_neg(float x)
 {
-    const float p = x * (1.f - x * (1.f / 2.f) * (1.f - x * (1.f / 3.f) * (1.f - x * (1.f / 4.f) *
-                        (1.f - x * (1.f / 5.f) * (1.f - x * (1.f / 6.f) * (1.f - x * (1.f / 7.f)))))));
+    const float g = fmaf(fmaf(fmaf(fmaf(fmaf(-1.f / 5040.f, x, 1.f / 720.f), x, -1.f / 120.f), x, 1.f / 24.f), x,
+                         -1.f / 6.f), x, 0.5f);
+    const float p = x * fmaf(g, -x, 1.f);
     const float q = 1.f - exp_neg(x);
     return x < 0.25f ? p : q;
 }
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
     const float2* __restrict__ fy = A.faces + (nx + 1);
     const float2* __restrict__ fz = A.faces + (nx + 1) + (ny + 1);
     double* __restrict__ absorbed = A.absorbed;
-    const int step_min = A.step_min > 0 ? A.step_min : 16;
+    const int step_min = A.step_min > 0 ? A.step_min : 20;
 
     // ---- stepping state (registers)
     int mode = M_NONE;
