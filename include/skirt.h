@@ -235,7 +235,9 @@ int skirt_dust_mass(skirt_grid_t grid, float* mass, void* stream);
  * wavelengths j in band b, 32 bands log-spaced over [min, max] of lambda_in;
  * T(m) = sum_b B_b(m), features(m, b) = log10(max(B_b, 1e-6 T / 32) / M)
  * (a band without absorbed power sits 6 dex below the cell's total; cells
- * without dust or absorbed power get -30), total(m) = T(m).  absorbed: device double[ncell][n_in];
+ * without dust or absorbed power get -30), total(m) = T(m).  B_b and T are
+ * summed in FP64 (T exact to FP64 rounding); the features are formed in FP32
+ * from B_b truncated to FP32 (a few FP32 ulp).  absorbed: device double[ncell][n_in];
  * lambda_in: host double[n_in] (micron, > 0); mass: device float[ncell];
  * features: device float[ncell][32]; total: device double[ncell]. */
 int skirt_band_features(const double* absorbed, long long ncell, int n_in, const double* lambda_in,

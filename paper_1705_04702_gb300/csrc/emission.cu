@@ -93,36 +93,93 @@ __global__ void dust_mass_kernel(const float* __restrict__ kr, long long n, floa
         mass[m] = kr[m] * vol;
 }
 
-// band b covers the input wavelengths [start[b], start[b+1]) (sorted input grid)
-__global__ void band_features_kernel(const double* __restrict__ A, long long ncell, int n_in,
-                                     const int* __restrict__ start, const float* __restrict__ mass,
-                                     float* __restrict__ features, double* __restrict__ total)
+// FP64 -> FP32 by truncation of the significand, on the integer pipe (GB300
+// retires FP64 and conversion instructions slowly); values below the FP32
+// normal range map to zero, values above it take the ordinary conversion.
+__device__ __forceinline__ float narrow_trunc(double x)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((u >> 52) & 0x7FF) - 1023 + 127;
+    if (e >= 255) return (float)x;
+    if (e <= 0) return 0.f;
+    return __uint_as_float((unsigned)(u >> 32 & 0x80000000u) | ((unsigned)e << 23) | (unsigned)((u >> 29) & 0x7FFFFFu));
+}
+
+// band b covers the input wavelengths [start[b], start[b+1]) (sorted input
+// grid).  One cell per lane, 32 cells per warp pass.  The warp walks the
+// input wavelengths in order in blocks of 32 columns; each block of its 32
+// rows is staged in shared memory with coalesced loads (one 256-byte row
+// segment per load).  Each lane sums its row's bands in wavelength order
+// (FP64) and, as the walk passes each band's end, adds the band sum to the
+// cell's total (FP64, band order): per cell about n_in/32 + 1 FP64 warp
+// instructions, which bound this kernel on GB300.  The features are formed
+// in FP32 and leave through a shared-memory transpose as coalesced rows.
+constexpr int BF_WARPS = 2;  // warps per block
+static_assert(NB == 32, "32 bands");
+
+__global__ void __launch_bounds__(32 * BF_WARPS) band_features_kernel(
+    const double* __restrict__ A, long long ncell, int n_in, const int* __restrict__ start,
+    const float* __restrict__ mass, float* __restrict__ features, double* __restrict__ total)
 {
     __shared__ int s_start[NB + 1];
+    __shared__ double s_tile[BF_WARPS][32][33];  // staged column block [row][column], one padding column
+    __shared__ float s_band[BF_WARPS][32][33];   // band sums, then features [row][band]
     for (int b = threadIdx.x; b <= NB; b += blockDim.x) s_start[b] = start[b];
     __syncthreads();
-    for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < ncell;
-         m += (long long)gridDim.x * blockDim.x) {
-        const double* row = A + (size_t)m * n_in;
-        const double M = (double)mass[m];
-        double B[NB], tot = 0.0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double (*tile)[33] = s_tile[warp];
+    float (*band)[33] = s_band[warp];
+    for (long long base = ((long long)blockIdx.x * BF_WARPS + warp) * 32; base < ncell;
+         base += (long long)gridDim.x * BF_WARPS * 32) {
+        const int nrow = ncell - base < 32 ? (int)(ncell - base) : 32;
+        int b = 0;
+        double sb = 0.0, tot = 0.0;
+        for (int c0 = 0; c0 < n_in; c0 += 32) {
+            const bool col_ok = c0 + lane < n_in;
+            double v[32];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            double s = 0.0;
-            for (int j = s_start[b]; j < s_start[b + 1]; ++j) s += row[j];
-            B[b] = s;
-            tot += s;
+            for (int rr = 0; rr < 32; ++rr)
+                v[rr] = (rr < nrow && col_ok) ? __ldcs(A + (size_t)(base + rr) * n_in + c0 + lane) : 0.0;
+            __syncwarp();
+#pragma unroll
+            for (int rr = 0; rr < 32; ++rr) tile[rr][lane] = v[rr];
+            __syncwarp();
+            const int cend = n_in - c0 < 32 ? n_in - c0 : 32;
+            for (int jj = 0; jj < cend; ++jj) {
+                // close the bands that end before this column (empty ones included)
+                while (b < NB && s_start[b + 1] <= c0 + jj) {
+                    band[lane][b] = narrow_trunc(sb);
+                    tot += sb;
+                    sb = 0.0;
+                    ++b;
+                }
+                sb += tile[lane][jj];
+            }
         }
+        for (; b < NB; ++b) {
+            band[lane][b] = narrow_trunc(sb);
+            tot += sb;
+            sb = 0.0;
+        }
+        const long long r = base + lane;
+        const float M = lane < nrow ? mass[r] : 0.f;
+        const float fl = 1e-6f * narrow_trunc(tot) / NB;
+        const bool ok = M > 0.f && tot > 0.0;
         // an empty band sits 6 dex (per band) below the cell's total power
-        const bool ok = M > 0.0 && tot > 0.0;
-        const double floor_b = 1e-6 * tot / NB;
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            const double pm = ok ? fmax(B[b], floor_b) / M : 0.0;
-            features[(size_t)m * NB + b] = log10f(fmaxf((float)fmax(pm, 1e-30), 1e-30f));
-        }
-        total[m] = tot;
+        for (int k = 0; k < NB; ++k)
+            band[lane][k] = log10f(fmaxf(ok ? fmaxf(band[lane][k], fl) / M : 0.f, 1e-30f));
+        if (lane < nrow) total[r] = tot;
+        __syncwarp();
+        for (int rr = 0; rr < nrow; ++rr) features[(size_t)(base + rr) * NB + lane] = band[rr][lane];
+        __syncwarp();
     }
+}
+
+int band_blocks(long long ncell)
+{
+    long long b = (ncell + 32 * BF_WARPS - 1) / (32 * BF_WARPS);
+    if (b > 152LL * 16) b = 152LL * 16;
+    return (int)(b < 1 ? 1 : b);
 }
 
 // G_i(T) = sum_l K_il / expm1(a_l / T) and T dG/dT = sum K_il q x (1 + q)
@@ -203,6 +260,101 @@ __global__ void exact_kernel(const double* __restrict__ A, int n_in, const doubl
             out[l] = e;
         }
         if (temperature)
+            for (int i = 0; i < NPOP; ++i) temperature[(size_t)m * NPOP + i] = (float)T[i];
+    }
+}
+
+// Warp-per-row form of exact_kernel, for short row lists (the surrogate's
+// fallback rows): the lanes split the wavelength sums, and every sum is
+// reduced and broadcast so that the Newton iteration stays warp-uniform.  Same
+// arithmetic as exact_kernel up to the order of the FP64 sums.
+__device__ __forceinline__ double warp_sum_bcast(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return __shfl_sync(0xffffffffu, v, 0);
+}
+
+__device__ void pop_G_warp(int i, double T, double& G, double& D, int lane)
+{
+    double g = 0.0, d = 0.0;
+    for (int l = lane; l < NOUT; l += 32) {
+        const double x = c_a[l] / T;
+        if (x > 700.0) continue;
+        const double q = 1.0 / expm1(x);
+        const double t = c_K[i][l] * q;
+        g += t;
+        d += t * x * (1.0 + q);
+    }
+    G = warp_sum_bcast(g);
+    D = warp_sum_bcast(d);
+}
+
+__device__ double solve_T_warp(int i, double ln_ratio, int lane)
+{
+    const double target = ln_ratio - c_lnc[i];
+    if (c_lnG_lo[i] - target >= 0.0) return T_LO;
+    if (c_lnG_hi[i] - target <= 0.0) return T_HI;
+    double lo = log(T_LO), hi = log(T_HI);
+    double y = log(T_REF) + ln_ratio / (4.0 + c_beta[i]);
+    if (!(y > lo && y < hi)) y = 0.5 * (lo + hi);
+    for (int it = 0; it < 100; ++it) {
+        double G, D;
+        pop_G_warp(i, exp(y), G, D, lane);
+        const double f = log(G) - target;
+        if (f < 0.0) lo = y; else hi = y;
+        double y_new = y - f * G / D;
+        if (!(y_new > lo && y_new < hi)) y_new = 0.5 * (lo + hi);
+        const bool done = fabs(y_new - y) <= 1e-13 * fabs(y);
+        y = y_new;
+        if (done) break;
+    }
+    return exp(y);
+}
+
+__global__ void exact_warp_kernel(const double* __restrict__ A, int n_in, const double* __restrict__ w,
+                                  const float* __restrict__ mass, const unsigned* __restrict__ rows,
+                                  long long nrows, double* __restrict__ emission, float* __restrict__ temperature)
+{
+    const int lane = threadIdx.x & 31;
+    for (long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nrows;
+         k += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const long long m = rows ? (long long)rows[k] : k;
+        const double* row = A + (size_t)m * n_in;
+        double p0 = 0.0, p1 = 0.0, p2 = 0.0;
+        for (int j = lane; j < n_in; j += 32) {
+            const double a = row[j];
+            p0 += __ldg(w + j) * a;
+            p1 += __ldg(w + n_in + j) * a;
+            p2 += __ldg(w + 2 * n_in + j) * a;
+        }
+        const double P[NPOP] = {warp_sum_bcast(p0), warp_sum_bcast(p1), warp_sum_bcast(p2)};
+        const double M = (double)mass[m];
+        double T[NPOP], S[NPOP];
+#pragma unroll
+        for (int i = 0; i < NPOP; ++i) {
+            T[i] = 0.0;
+            S[i] = 0.0;
+            if (P[i] > 0.0 && M > 0.0) {
+                T[i] = solve_T_warp(i, log(P[i] / M), lane);
+                double G, D;
+                pop_G_warp(i, T[i], G, D, lane);
+                S[i] = G;
+            }
+        }
+        double* out = emission + (size_t)m * NOUT;
+        for (int l = lane; l < NOUT; l += 32) {
+            double e = 0.0;
+#pragma unroll
+            for (int i = 0; i < NPOP; ++i) {
+                if (S[i] > 0.0) {
+                    const double x = c_a[l] / T[i];
+                    if (x <= 700.0) e += P[i] * (c_K[i][l] / expm1(x)) / S[i];
+                }
+            }
+            out[l] = e;
+        }
+        if (temperature && lane == 0)
             for (int i = 0; i < NPOP; ++i) temperature[(size_t)m * NPOP + i] = (float)T[i];
     }
 }
@@ -308,8 +460,13 @@ int launch_exact_emission(const double* absorbed, int n_in, const double* w_dev,
                           cudaStream_t s)
 {
     ECK(upload_model(s));
-    if (nrows > 0) exact_kernel<<<grid_blocks(nrows, 128), 128, 0, s>>>(absorbed, n_in, w_dev, mass, rows, nrows,
-                                                                      emission, temperature);
+    // a short row list: one warp per row keeps the Newton solves' latency short
+    if (rows && nrows > 0 && nrows <= 8192)
+        exact_warp_kernel<<<(int)((nrows + 3) / 4), 128, 0, s>>>(absorbed, n_in, w_dev, mass, rows, nrows, emission,
+                                                                temperature);
+    else if (nrows > 0)
+        exact_kernel<<<grid_blocks(nrows, 128), 128, 0, s>>>(absorbed, n_in, w_dev, mass, rows, nrows, emission,
+                                                             temperature);
     ECK(cudaGetLastError());
     return SKIRT_OK;
 }
@@ -351,7 +508,7 @@ extern "C" int skirt_band_features(const double* absorbed, long long ncell, int 
     int* d_start = nullptr;
     ECK(cudaMallocAsync((void**)&d_start, sizeof(int) * (NB + 1), s));
     ECK(cudaMemcpyAsync(d_start, start.data(), sizeof(int) * (NB + 1), cudaMemcpyHostToDevice, s));
-    band_features_kernel<<<grid_blocks(ncell, 128), 128, 0, s>>>(absorbed, ncell, n_in, d_start, mass, features, total);
+    band_features_kernel<<<band_blocks(ncell), 32 * BF_WARPS, 0, s>>>(absorbed, ncell, n_in, d_start, mass, features, total);
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(d_start, s);
     if (e != cudaSuccess) return set_error(SKIRT_ERR_CUDA, "band features: %s", cudaGetErrorString(e));
@@ -404,7 +561,7 @@ extern "C" int skirt_dust_emission(const double* absorbed, long long ncell, int 
         ECK(cudaMemcpyAsync(d_start, start.data(), sizeof(int) * (NB + 1), cudaMemcpyHostToDevice, s));
         if (temperature) zero_temperature_kernel<<<grid_blocks(3 * ncell, 256), 256, 0, s>>>(temperature, 3 * ncell);
         ECK(cudaEventRecord(ev[0], s));
-        band_features_kernel<<<grid_blocks(ncell, 128), 128, 0, s>>>(absorbed, ncell, n_in, d_start, mass, d_feat, d_tot);
+        band_features_kernel<<<band_blocks(ncell), 32 * BF_WARPS, 0, s>>>(absorbed, ncell, n_in, d_start, mass, d_feat, d_tot);
         ECK(cudaGetLastError());
         ECK(cudaEventRecord(ev[1], s));
         rc = mlp_forward_internal(net, d_feat, d_tot, ncell, emission, d_flag, s);

@@ -46,18 +46,22 @@ static_assert(OFF_B3 + NO == NPARAM, "packed parameter layout");
 // --------------------------------------------------------------------------
 // inference
 // --------------------------------------------------------------------------
-constexpr int INF_WARPS = 4;
+constexpr int INF_WARPS = 8;
 constexpr int INF_ROWS = 16 * INF_WARPS;
-// shared memory: W1 [128][32], W2 [128][128], W3 [104][128] (bf16), biases
-// [128 + 128 + 104] (fp32), mean / inv_std / lo / hi [32] each, per-warp
-// feature staging [16][32] fp32
+// shared memory: W1 [128][32], W2 [128][128], W3 [104][128] (bf16) with
+// every row padded by 8 elements, so that the eight rows one fragment load
+// touches start 4 banks apart (conflict-free); biases [128 + 128 + 104]
+// (fp32); mean / inv_std / lo / hi [32] each; per-warp feature staging
+// [16][33] fp32 (one padding column, conflict-free column reads)
+constexpr int KP1 = NIN + 8, KP2 = NH + 8, XP = NIN + 1;
 constexpr size_t SM_W1 = 0;
-constexpr size_t SM_W2 = SM_W1 + sizeof(uint16_t) * NH * NIN;
-constexpr size_t SM_W3 = SM_W2 + sizeof(uint16_t) * NH * NH;
-constexpr size_t SM_B = SM_W3 + sizeof(uint16_t) * NO_PAD * NH;
+constexpr size_t SM_W2 = SM_W1 + sizeof(uint16_t) * NH * KP1;
+constexpr size_t SM_W3 = SM_W2 + sizeof(uint16_t) * NH * KP2;
+constexpr size_t SM_B = SM_W3 + sizeof(uint16_t) * NO_PAD * KP2;
 constexpr size_t SM_ST = SM_B + sizeof(float) * (NH + NH + NO_PAD);
 constexpr size_t SM_X = SM_ST + sizeof(float) * 4 * NIN;
-constexpr size_t SM_TOTAL = SM_X + sizeof(float) * INF_WARPS * 16 * NIN;
+constexpr size_t SM_TOTAL = SM_X + sizeof(float) * INF_WARPS * 16 * XP;
+static_assert((KP1 * 2) % 16 == 0 && (KP2 * 2) % 16 == 0, "padded rows keep 16-byte alignment");
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
@@ -75,7 +79,19 @@ __device__ __forceinline__ void mma_bf16(float* c, uint32_t a0, uint32_t a1, uin
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float silu_f(float z) { return z / (1.f + __expf(-z)); }
+__device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.f + __expf(-z)); }
+
+// FP32 -> FP64 for a non-negative float by IEEE-754 field manipulation on the
+// integer pipe (exact for normal floats; zero and subnormals map to zero), so
+// that the epilogue issues no FP64-pipe instruction; infinities, NaN and
+// negative values take the ordinary conversion
+__device__ __forceinline__ double widen_pos(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = u >> 23;
+    if (e >= 255u) return (double)f;
+    return e ? __hiloint2double((int)((u >> 3) + 0x38000000u), (int)(u << 29)) : 0.0;
+}
 
 // acc[j][0..3] for n-tiles j: rows (g, g+8), cols 8j + 2t + {0,1}; produces
 // the next layer's A fragments: k-tile kk from n-tiles 2kk, 2kk+1
@@ -92,11 +108,12 @@ __device__ __forceinline__ void to_afrag(const float (&acc)[NT][4], uint32_t (&a
 }
 
 // one layer: out[NT] n-tiles = A (KT k-tiles) x W^T, W [rows = 8*NT][cols = 16*KT] bf16 in smem
-template <int NT, int KT>
+// with row stride KP elements
+template <int NT, int KT, int KP>
 __device__ __forceinline__ void layer(const uint32_t (&a)[KT][4], const uint16_t* __restrict__ W,
                                       const float* __restrict__ bias, float (&out)[NT][4], int g, int t)
 {
-    constexpr int K = 16 * KT;
+    constexpr int K = KP;
 #pragma unroll
     for (int j = 0; j < NT; ++j) {
         const float b0 = bias[8 * j + 2 * t], b1 = bias[8 * j + 2 * t + 1];
@@ -111,7 +128,7 @@ __device__ __forceinline__ void layer(const uint32_t (&a)[KT][4], const uint16_t
     }
 }
 
-__global__ void __launch_bounds__(32 * INF_WARPS) mlp_infer_kernel(
+__global__ void __launch_bounds__(32 * INF_WARPS, 2) mlp_infer_kernel(
     const uint16_t* __restrict__ Wg, const float* __restrict__ Bg, const float* __restrict__ stats,
     const float* __restrict__ features, const double* __restrict__ total, long long n,
     double* __restrict__ emission, unsigned char* __restrict__ flags)
@@ -119,10 +136,17 @@ __global__ void __launch_bounds__(32 * INF_WARPS) mlp_infer_kernel(
     extern __shared__ __align__(16) unsigned char sm[];
     // stage the weights (bf16, contiguous W1 W2 W3) and biases / statistics
     {
-        const int nw = (NH * NIN + NH * NH + NO_PAD * NH) / 8;  // 16-byte chunks
+        // 16-byte chunks of the contiguous global rows into the padded rows
         const uint4* src = reinterpret_cast<const uint4*>(Wg);
-        uint4* dst = reinterpret_cast<uint4*>(sm + SM_W1);
-        for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
+        constexpr int c1 = NIN / 8, c2 = NH / 8;  // chunks per row
+        for (int i = threadIdx.x; i < NH * c1; i += blockDim.x)
+            *reinterpret_cast<uint4*>(sm + SM_W1 + sizeof(uint16_t) * ((i / c1) * KP1 + 8 * (i % c1))) = src[i];
+        src += NH * c1;
+        for (int i = threadIdx.x; i < NH * c2; i += blockDim.x)
+            *reinterpret_cast<uint4*>(sm + SM_W2 + sizeof(uint16_t) * ((i / c2) * KP2 + 8 * (i % c2))) = src[i];
+        src += NH * c2;
+        for (int i = threadIdx.x; i < NO_PAD * c2; i += blockDim.x)
+            *reinterpret_cast<uint4*>(sm + SM_W3 + sizeof(uint16_t) * ((i / c2) * KP2 + 8 * (i % c2))) = src[i];
         float* sb = reinterpret_cast<float*>(sm + SM_B);
         for (int i = threadIdx.x; i < NH + NH + NO_PAD; i += blockDim.x) sb[i] = Bg[i];
         float* ss = reinterpret_cast<float*>(sm + SM_ST);
@@ -141,14 +165,14 @@ __global__ void __launch_bounds__(32 * INF_WARPS) mlp_infer_kernel(
     const float* hhi = hlo + NIN;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, t = lane & 3;
-    float* xs = reinterpret_cast<float*>(sm + SM_X) + warp * 16 * NIN;
+    float* xs = reinterpret_cast<float*>(sm + SM_X) + warp * 16 * XP;
 
     for (long long base = (long long)blockIdx.x * INF_ROWS + warp * 16; base < n;
          base += (long long)gridDim.x * INF_ROWS) {
         // ---- features of 16 rows: coalesced load, hull check, standardise
         for (int i = lane; i < 16 * NIN; i += 32) {
             const long long r = base + i / NIN;
-            xs[i] = r < n ? features[r * NIN + (i % NIN)] : 0.f;
+            xs[(i / NIN) * XP + (i % NIN)] = r < n ? features[r * NIN + (i % NIN)] : 0.f;
         }
         __syncwarp();
         if (lane < 16 && flags) {
@@ -156,7 +180,7 @@ __global__ void __launch_bounds__(32 * INF_WARPS) mlp_infer_kernel(
             if (r < n) {
                 bool out = false;
                 for (int k = 0; k < NIN; ++k) {
-                    const float v = xs[lane * NIN + k];
+                    const float v = xs[lane * XP + k];
                     out |= !(v >= hlo[k] && v <= hhi[k]);
                 }
                 // a cell without absorbed power emits nothing: no fallback needed
@@ -167,7 +191,7 @@ __global__ void __launch_bounds__(32 * INF_WARPS) mlp_infer_kernel(
 #pragma unroll
         for (int kk = 0; kk < 2; ++kk) {
             const int c = 16 * kk + 2 * t;
-            auto sx = [&](int row, int col) { return (xs[row * NIN + col] - mean[col]) * istd[col]; };
+            auto sx = [&](int row, int col) { return (xs[row * XP + col] - mean[col]) * istd[col]; };
             a1[kk][0] = pack_bf16(sx(g, c), sx(g, c + 1));
             a1[kk][1] = pack_bf16(sx(g + 8, c), sx(g + 8, c + 1));
             a1[kk][2] = pack_bf16(sx(g, c + 8), sx(g, c + 9));
@@ -176,13 +200,13 @@ __global__ void __launch_bounds__(32 * INF_WARPS) mlp_infer_kernel(
         __syncwarp();
         // ---- layers
         float h[NH / 8][4];
-        layer<NH / 8, 2>(a1, W1, B1, h, g, t);
+        layer<NH / 8, 2, KP1>(a1, W1, B1, h, g, t);
         uint32_t a2[NH / 16][4];
         to_afrag<NH / 8>(h, a2);
-        layer<NH / 8, NH / 16>(a2, W2, B2, h, g, t);
+        layer<NH / 8, NH / 16, KP2>(a2, W2, B2, h, g, t);
         to_afrag<NH / 8>(h, a2);
         float z[NO_PAD / 8][4];
-        layer<NO_PAD / 8, NH / 16>(a2, W3, B3, z, g, t);
+        layer<NO_PAD / 8, NH / 16, KP2>(a2, W3, B3, z, g, t);
         // ---- softmax over the 100 outputs of rows g and g+8 (4 lanes per row)
         float m0 = -3.0e38f, m1 = -3.0e38f;
 #pragma unroll
@@ -208,19 +232,21 @@ __global__ void __launch_bounds__(32 * INF_WARPS) mlp_infer_kernel(
         s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
         s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
         s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+        // emission = shape x absorbed power, formed in FP32 (the shape is an FP32
+        // softmax) and widened exactly to FP64
         const long long r0 = base + g, r1 = base + g + 8;
-        const double f0 = r0 < n ? total[r0] / (double)s0 : 0.0;
-        const double f1 = r1 < n ? total[r1] / (double)s1 : 0.0;
+        const float f0 = r0 < n ? (float)total[r0] / s0 : 0.f;
+        const float f1 = r1 < n ? (float)total[r1] / s1 : 0.f;
 #pragma unroll
         for (int j = 0; j < NO_PAD / 8; ++j) {
             const int c = 8 * j + 2 * t;
             if (c < NO) {
                 if (r0 < n)
-                    *reinterpret_cast<double2*>(emission + r0 * NO + c) =
-                        make_double2(f0 * (double)z[j][0], f0 * (double)z[j][1]);
+                    __stcs(reinterpret_cast<double2*>(emission + r0 * NO + c),
+                           make_double2(widen_pos(f0 * z[j][0]), widen_pos(f0 * z[j][1])));
                 if (r1 < n)
-                    *reinterpret_cast<double2*>(emission + r1 * NO + c) =
-                        make_double2(f1 * (double)z[j][2], f1 * (double)z[j][3]);
+                    __stcs(reinterpret_cast<double2*>(emission + r1 * NO + c),
+                           make_double2(widen_pos(f1 * z[j][2]), widen_pos(f1 * z[j][3])));
             }
         }
     }
