@@ -47,6 +47,7 @@ static_assert(OFF_B3 + NO == NPARAM, "packed parameter layout");
 // inference
 // --------------------------------------------------------------------------
 constexpr int INF_WARPS = 8;
+constexpr int SPLIT_MAX = 160;  // split-K slices of a weight-gradient product
 constexpr int INF_ROWS = 16 * INF_WARPS;
 // shared memory: W1 [128][32], W2 [128][128], W3 [104][128] (bf16) with
 // every row padded by 8 elements, so that the eight rows one fragment load
@@ -258,20 +259,25 @@ __global__ void __launch_bounds__(32 * INF_WARPS, 2) mlp_infer_kernel(
 // C[M][N] = op(A)[M][K] op(B)[K][N]; A is [M][K] (ta = 0) or [K][M] (ta = 1);
 // B is [K][N] (tb = 0) or [N][K] (tb = 1); all row-major.  64 x 64 tiles,
 // 256 threads, 4 x 4 outputs each.
+// With gridDim.z = S > 1 (split K), block z sums k in [z Kc, (z+1) Kc) and
+// writes its partial product to C + z M N; split_reduce_kernel adds the S
+// partials in order.
 __global__ void gemm_kernel(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ C, int M,
-                            int N, int K, int ta, int tb)
+                            int N, int K, int ta, int tb, int Kc)
 {
     __shared__ float As[16][65], Bs[16][65];
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    const int kb = blockIdx.z * Kc, ke = min(K, kb + Kc);
+    C += (size_t)blockIdx.z * M * N;
     float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int k0 = kb; k0 < ke; k0 += 16) {
         for (int i = threadIdx.x; i < 16 * 64; i += 256) {
             const int kk = i / 64, mm = i % 64;
             const int gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < M && gk < K) ? (ta ? A[(size_t)gk * M + gm] : A[(size_t)gm * K + gk]) : 0.f;
+            As[kk][mm] = (gm < M && gk < ke) ? (ta ? A[(size_t)gk * M + gm] : A[(size_t)gm * K + gk]) : 0.f;
             const int gn = n0 + mm;
-            Bs[kk][mm] = (gn < N && gk < K) ? (tb ? B[(size_t)gn * K + gk] : B[(size_t)gk * N + gn]) : 0.f;
+            Bs[kk][mm] = (gn < N && gk < ke) ? (tb ? B[(size_t)gn * K + gk] : B[(size_t)gk * N + gn]) : 0.f;
         }
         __syncthreads();
 #pragma unroll
@@ -293,6 +299,16 @@ __global__ void gemm_kernel(const float* __restrict__ A, const float* __restrict
             const int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
             if (gm < M && gn < N) C[(size_t)gm * N + gn] = acc[i][j];
         }
+}
+
+// C[i] = sum over z < S of part[z][i], in order (deterministic split-K)
+__global__ void split_reduce_kernel(const float* __restrict__ part, float* __restrict__ C, int mn, int S)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < mn; i += gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int z = 0; z < S; ++z) acc += part[(size_t)z * mn + i];
+        C[i] = acc;
+    }
 }
 
 // z += bias (per column); a = silu(z)
@@ -649,9 +665,11 @@ namespace {
 struct Work {
     float *xb = nullptr, *tb = nullptr, *z1 = nullptr, *a1 = nullptr, *z2 = nullptr, *a2 = nullptr, *z3 = nullptr,
           *d3 = nullptr, *da = nullptr, *d = nullptr, *loss = nullptr;
+    float* part = nullptr;  // split-K partial products of the weight gradients
     cudaError_t alloc(int B, cudaStream_t s)
     {
         cudaError_t e;
+        if ((e = cudaMallocAsync((void**)&part, sizeof(float) * SPLIT_MAX * NH * NH, s))) return e;
         if ((e = cudaMallocAsync((void**)&xb, sizeof(float) * B * NIN, s))) return e;
         if ((e = cudaMallocAsync((void**)&tb, sizeof(float) * B * NO, s))) return e;
         if ((e = cudaMallocAsync((void**)&z1, sizeof(float) * B * NH, s))) return e;
@@ -666,7 +684,7 @@ struct Work {
     }
     void release(cudaStream_t s)
     {
-        for (float* p : {xb, tb, z1, a1, z2, a2, z3, d3, da, d, loss})
+        for (float* p : {xb, tb, z1, a1, z2, a2, z3, d3, da, d, loss, part})
             if (p) cudaFreeAsync(p, s);
     }
 };
@@ -674,7 +692,23 @@ struct Work {
 void gemm(const float* A, const float* B, float* C, int M, int N, int K, int ta, int tb, cudaStream_t s)
 {
     dim3 grid((N + 63) / 64, (M + 63) / 64);
-    gemm_kernel<<<grid, 256, 0, s>>>(A, B, C, M, N, K, ta, tb);
+    gemm_kernel<<<grid, 256, 0, s>>>(A, B, C, M, N, K, ta, tb, K);
+}
+
+// weight gradient C[M][N] = A^T B over the batch (K = batch rows): few output
+// tiles and a long K, so K is split across blocks (at least ~2 blocks per SM)
+// with a deterministic reduction of the partials
+void gemm_wgrad(const float* A, const float* B, float* C, int M, int N, int K, float* part, cudaStream_t s)
+{
+    const int tiles = ((N + 63) / 64) * ((M + 63) / 64);
+    int S = (304 + tiles - 1) / tiles;
+    if (S > SPLIT_MAX) S = SPLIT_MAX;
+    int Kc = (K + S - 1) / S;
+    Kc = (Kc + 15) & ~15;
+    S = (K + Kc - 1) / Kc;
+    dim3 grid((N + 63) / 64, (M + 63) / 64, S);
+    gemm_kernel<<<grid, 256, 0, s>>>(A, B, part, M, N, K, 1, 0, Kc);
+    split_reduce_kernel<<<(M * N + 255) / 256, 256, 0, s>>>(part, C, M * N, S);
 }
 
 // forward + backward of one batch already in w.xb / w.tb; gradient into net->G, loss added to *w.loss
@@ -689,17 +723,17 @@ void fwd_bwd(skirt_mlp_s* net, Work& w, int B, cudaStream_t s)
     gemm(w.a2, P + OFF_W3, w.z3, B, NO, NH, 0, 1, s);
     softmax_xent_kernel<<<(B * 32 + 255) / 256, 256, 0, s>>>(w.z3, P + OFF_B3, w.tb, w.d3, B, w.loss);
     // layer 3
-    gemm(w.d3, w.a2, G + OFF_W3, NO, NH, B, 1, 0, s);
+    gemm_wgrad(w.d3, w.a2, G + OFF_W3, NO, NH, B, w.part, s);
     colsum_kernel<<<NO, 256, 0, s>>>(w.d3, G + OFF_B3, B, NO);
     gemm(w.d3, P + OFF_W3, w.da, B, NH, NO, 0, 0, s);
     silu_back_kernel<<<blocks_for((long long)B * NH, 256), 256, 0, s>>>(w.z2, w.da, w.d, (long long)B * NH);
     // layer 2
-    gemm(w.d, w.a1, G + OFF_W2, NH, NH, B, 1, 0, s);
+    gemm_wgrad(w.d, w.a1, G + OFF_W2, NH, NH, B, w.part, s);
     colsum_kernel<<<NH, 256, 0, s>>>(w.d, G + OFF_B2, B, NH);
     gemm(w.d, P + OFF_W2, w.da, B, NH, NH, 0, 0, s);
     silu_back_kernel<<<blocks_for((long long)B * NH, 256), 256, 0, s>>>(w.z1, w.da, w.d, (long long)B * NH);
     // layer 1
-    gemm(w.d, w.xb, G + OFF_W1, NH, NIN, B, 1, 0, s);
+    gemm_wgrad(w.d, w.xb, G + OFF_W1, NH, NIN, B, w.part, s);
     colsum_kernel<<<NH, 256, 0, s>>>(w.d, G + OFF_B1, B, NH);
 }
 
