@@ -11,10 +11,11 @@ before every timed step.
 
 Reported next to it: the plain FP64 form on 1e7 packets of the same
 workload, the end-to-end time through the C ABI with pinned host buffers,
-the roofline of the trace kernel, and the CPU FP64 oracle timed on a sample.
+the rooflines of the trace kernel (HBM bytes and FP64 reductions), and the
+CPU FP64 oracle timed on a sample, on one core and on every host core.
 
 `--impl reference` times the oracle (the slow, plain CPU program the
-parity tests compare against) on the host cores instead.
+parity tests compare against) on every host core instead.
 """
 from __future__ import annotations
 
@@ -150,32 +151,92 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------ oracle on CPU
+def packet_lambdas(npk, lo, hi):
+    """Packet-wavelengths in packet range [lo, hi) of every wavelength."""
+    return int(np.clip(np.minimum(npk.astype(np.int64), hi) - lo, 0, None).sum())
+
+
+def _oracle_serve(spec, tasks, done):
+    """Worker process: builds the workload once, then traces the packet
+    ranges it is sent with the unmodified oracle and reports the
+    packet-wavelengths it traced."""
+    import oracle
+    prob = workload(argparse.Namespace(**spec))
+    done.put(0)
+    while True:
+        r = tasks.get()
+        if r is None:
+            break
+        oracle.trace(prob, r[0], r[1])
+        done.put(packet_lambdas(prob.npk, r[0], r[1]))
+
+
+class OraclePool:
+    """The oracle on every host core: one spawned process per core (started
+    before any GPU work), each tracing its own packet range of a step."""
+
+    def __init__(self, args, cores=None):
+        import multiprocessing as mp
+        import oracle
+        oracle.build()
+        self.cores = cores or os.cpu_count() or 1
+        ctx = mp.get_context("spawn")
+        spec = {"workload": args.workload, "packets": args.packets, "grid": args.grid}
+        self.tasks = [ctx.Queue() for _ in range(self.cores)]
+        self.done = ctx.Queue()
+        self.procs = [ctx.Process(target=_oracle_serve, args=(spec, q, self.done), daemon=True) for q in self.tasks]
+        for p in self.procs:
+            p.start()
+        for _ in self.procs:
+            self.done.get()
+
+    def step(self, lo, per_core):
+        """Packets [lo + i per_core, lo + (i + 1) per_core) on core i; returns
+        (packet-wavelengths traced, wall seconds)."""
+        t0 = time.perf_counter()
+        for i, q in enumerate(self.tasks):
+            q.put((lo + i * per_core, lo + (i + 1) * per_core))
+        n = sum(self.done.get() for _ in self.tasks)
+        return n, time.perf_counter() - t0
+
+    def close(self):
+        for q in self.tasks:
+            q.put(None)
+        for p in self.procs:
+            p.join(timeout=30)
+
+
 # ------------------------------------------------------------------ reference
 def run_reference(args):
-    """The CPU FP64 oracle on a bounded sample per step (rank 0 only)."""
+    """The CPU FP64 oracle on every host core, a bounded sample per step (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import oracle
-    oracle.build()
     prob = workload(args)
-    per_step = max(1, min(8000, int(args.packets)))
+    pool = OraclePool(args)
+    per_core = max(1, min(20000, int(args.packets) // max(pool.cores * (args.warmup + args.steps), 1)))
+    lo = 0
     for _ in range(args.warmup):
-        oracle.trace(prob, 0, per_step)
-    t0 = time.perf_counter()
-    for s in range(args.steps):
-        lo = (s + 1) * per_step
-        oracle.trace(prob, lo, lo + per_step)
-    dt = time.perf_counter() - t0
-    value = per_step * args.steps / dt
+        pool.step(lo, per_core)
+        lo += pool.cores * per_core
+    n_tot, dt = 0, 0.0
+    for _ in range(args.steps):
+        n, t = pool.step(lo, per_core)
+        n_tot += n
+        dt += t
+        lo += pool.cores * per_core
+    pool.close()
+    value = n_tot / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": config_of(args, prob, {"sample_per_step": per_step}),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{per_step} packets per step of the {int(args.packets):.0e}-packet workload"},
+        "config": config_of(args, prob, {"sample_per_step": pool.cores * per_core}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+                         "sample": f"{pool.cores} processes x {per_core} packets of every wavelength per step "
+                                   f"(disjoint packet ranges) of the workload, single-threaded FP64 oracle each"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -218,14 +279,20 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        per = max(1, args.cpu_packets // prob.wl.n)  # packets per wavelength in the sample
-        n = int(np.minimum(prob.npk, per).sum())
+        per = max(1, args.cpu_packets // prob.wl.n)  # packets per wavelength per core
+        n1 = packet_lambdas(prob.npk, 0, per)
         t0 = time.perf_counter()
         oracle.trace(prob, 0, per)
-        dt = time.perf_counter() - t0
-        cpu = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"packets 0..{per - 1} of every wavelength ({n} packet-wavelengths) of the workload, "
-                         f"single-threaded FP64, {dt:.1f} s"}
+        dt1 = time.perf_counter() - t0
+        pool = OraclePool(args)
+        n, dt = pool.step(per, per)
+        pool.close()
+        cpu = {"value": n / dt, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+               "sample": f"{pool.cores} processes, each tracing its own {per} packets of every wavelength "
+                         f"({n} packet-wavelengths in all) with the single-threaded FP64 oracle, {dt:.1f} s wall",
+               "one_core": {"value": n1 / dt1, "unit": UNIT, "cores": 1,
+                            "sample": f"packets 0..{per - 1} of every wavelength ({n1} packet-wavelengths), "
+                                      f"{dt1:.1f} s"}}
 
     import torch
     from paper_1705_04702_gb300 import build
@@ -317,6 +384,16 @@ def main():
                            "peel_steps": led["peel_steps"] / packets,
                            "scatterings": led["scatterings"] / packets}}
 
+    # ---- atomic roofline: FP64 reductions per packet (one per deposit, one per
+    # peel-off tally) against the measured random red.f64 rate into a table
+    # the size of this absorbed table
+    red_rate, _ = S.skirt_microbench(3, grid.ncell * n)
+    atomics_pp = (led["deposit_steps"] + (packets + led["scatterings"]) * len(prob.instruments)) / packets
+    roof_atomic = {"bound": "atomics", "achieved": value / world * atomics_pp, "peak": red_rate,
+                   "unit": "red.f64/s", "frac": value / world * atomics_pp / red_rate,
+                   "atomics_per_packet": atomics_pp,
+                   "peak_source": f"measured in this run: random red.global.add.f64 into {grid.ncell * n} doubles"}
+
     # ---- plain FP64 form, one launch per wavelength, on a sample
     fp64 = None
     if args.fp64_packets > 0:
@@ -373,6 +450,7 @@ def main():
                                                  "block": opts.block, "chunk": opts.chunk,
                                                  "blocks_per_sm": opts.blocks_per_sm}}),
             "roofline": roof,
+            "roofline_atomic": roof_atomic,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps * (1 + len(prob.instruments)),
