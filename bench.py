@@ -373,9 +373,10 @@ def main():
     k_ms = float(np.mean(kernel_ms))
     achieved = per_launch_bytes / (k_ms / 1e3) / 1e9
     peak, peak_kind = peaks()
-    # DRAM bytes (read + write) of trace_mixed_kernel per launch from an ncu capture of the current
-    # kernel; None until one is taken
-    traffic = None
+    # DRAM bytes (read + write) per packet of trace_mixed_kernel on the 256^3 disk, from one ncu
+    # capture of a 3e6-packet launch (profiles/trace_mixed_kernel_disk256_3e6_full.md), scaled by
+    # the packets of this launch; None for other workloads
+    traffic = 30251.5 * packets if (args.workload == "disk" and args.grid == 256) else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_source": peak_kind, "kernel": "trace_mixed_kernel",
             "kernel_ms": k_ms, "algorithmic_bytes_per_launch": per_launch_bytes,
