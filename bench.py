@@ -242,6 +242,27 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ replicas
+def replica_seed(rank):
+    """Every rank traces its own packets: the Philox key differs per rank."""
+    return 1 + rank
+
+
+def job_time(elapsed, dist=None, device=None):
+    """Wall time of the whole job: the slowest rank's timed region."""
+    if dist is None:
+        return elapsed
+    import torch
+    t = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, steps, elapsed):
+    """Units all ranks processed per second of the slowest rank."""
+    return units_per_rank * world * steps / elapsed
+
+
 # ------------------------------------------------------------------ learned
 def run_learned_report(args):
     """The learned form on the clumpy torus (256^3, 200 wavelengths, then a
@@ -310,7 +331,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    seed = 1 + rank  # independent replicas: every rank traces its own packets
+    seed = replica_seed(rank)  # independent replicas: every rank traces its own packets
     prob.seed = seed
     grid = S.Grid(prob.grid)
     n = prob.wl.n
@@ -357,13 +378,9 @@ def main():
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    if dist is not None:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = job_time(ev0.elapsed_time(ev1) / 1e3, dist, "cuda")
     packets = prob.total_packets
-    value = packets * world * args.steps / elapsed
+    value = job_throughput(packets, world, args.steps, elapsed)
 
     # ---- roofline of the trace kernel: algorithmic bytes per launch
     kr_b = 4
