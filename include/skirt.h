@@ -306,6 +306,33 @@ int skirt_dust_emission(const double* absorbed, long long ncell, int n_in, const
                         const float* mass, int mode, skirt_mlp_t net, double* emission, float* temperature,
                         skirt_emission_stats* stats, void* stream);
 
+/* Per-wavelength luminosity of a dust emission table (Sect. 3.2: the dust
+ * cells are the sources of the dust emission phases): the column sums over
+ * the cells of emission [ncell][nlambda] (device doubles, ncell = the grid's
+ * cells), in FP64, into host totals[nlambda].  These are the source
+ * luminosities skirt_trace takes for a dust-cell source without lsrc, so a
+ * caller can give packets only to wavelengths that carry luminosity.  Uses
+ * the grid's scratch memory; synchronises the stream.  Errors: INVALID_ARG
+ * (also for negative or non-finite entries), OOM, CUDA. */
+int skirt_emission_totals(skirt_grid_t grid, const double* emission, int nlambda, double* totals, void* stream);
+
+/* Exact dust emission of cells heated by two absorbed fields on two
+ * wavelength grids (Sect. 3.2, dust self-absorption phase: each cycle's
+ * emission follows from the absorbed stellar radiation plus the absorbed
+ * emission of the dust itself, kept in a separate table).  The power each
+ * grain population absorbs adds:
+ * P_i(m) = sum_j w_i(lambda_a,j) A(m, j) + sum_l w_i(lambda_b,l) B(m, l),
+ * then the same equilibrium solve and emission rows as skirt_dust_emission
+ * in SKIRT_EMIT_EXACT mode (rows sum to P_0 + P_1 + P_2).
+ * absorbed_a: device double[ncell][n_a] on the host grid lambda_a;
+ * absorbed_b: device double[ncell][n_b] on lambda_b, or NULL with n_b = 0
+ * (then the result equals skirt_dust_emission's); mass: device float[ncell];
+ * emission: device double[ncell][100]; temperature: device float[ncell][3] or
+ * NULL.  Synchronises the stream on return.  Errors: INVALID_ARG, OOM, CUDA. */
+int skirt_dust_emission_pair(const double* absorbed_a, long long ncell, int n_a, const double* lambda_a,
+                             const double* absorbed_b, int n_b, const double* lambda_b, const float* mass,
+                             double* emission, float* temperature, void* stream);
+
 /* Exact emission without allocating (the paper has no counterpart: it is an
  * interface for callers that cannot allocate device memory at call time,
  * e.g. a process whose framework allocator has already reserved the device

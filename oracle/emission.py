@@ -130,12 +130,28 @@ def exact_emission(absorbed, lam_in, mass):
     mass [n_cell] -> emission [n_cell, 100], T [n_cell, 3], P [n_cell, 3].
     Cells with no dust or no absorbed power emit nothing (T = 0)."""
     absorbed = np.asarray(absorbed, dtype=np.float64)
+    P = absorbed @ absorption_shares(lam_in).T    # [n_cell, 3]
+    return emission_from_power(P, mass)
+
+
+def exact_emission_pair(absorbed_a, lam_a, absorbed_b, lam_b, mass):
+    """Exact emission of cells heated by two absorbed fields on two
+    wavelength grids, e.g. the stellar field and the dust's own emission
+    (Sect. 3.2, dust self-absorption phase): the power each population
+    absorbs adds, P = A w_a^T + B w_b^T."""
+    P = (np.asarray(absorbed_a, dtype=np.float64) @ absorption_shares(lam_a).T +
+         np.asarray(absorbed_b, dtype=np.float64) @ absorption_shares(lam_b).T)
+    return emission_from_power(P, mass)
+
+
+def emission_from_power(P, mass):
+    """Equilibrium temperatures and emission rows from the power P [n_cell, 3]
+    absorbed by each population and the dust mass [n_cell]."""
+    P = np.asarray(P, dtype=np.float64)
     mass = np.asarray(mass, dtype=np.float64)
     lam, W = emission_grid()
-    w = absorption_shares(lam_in)                 # [3, n_in]
-    P = absorbed @ w.T                            # [n_cell, 3]
-    emission = np.zeros((absorbed.shape[0], NOUT))
-    T = np.zeros((absorbed.shape[0], 3))
+    emission = np.zeros((P.shape[0], NOUT))
+    T = np.zeros((P.shape[0], 3))
     for i in range(3):
         ok = (P[:, i] > 0) & (mass > 0)
         if not ok.any():

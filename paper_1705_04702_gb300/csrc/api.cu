@@ -214,6 +214,19 @@ extern "C" int skirt_grid_create(skirt_grid_t* out, int nx, int ny, int nz, cons
     return SKIRT_OK;
 }
 
+extern "C" int skirt_emission_totals(skirt_grid_t g, const double* emission, int nlambda, double* totals,
+                                     void* stream)
+{
+    if (!g || !emission || !totals) return fail(SKIRT_ERR_INVALID_ARG, "grid / emission / totals is NULL");
+    if (nlambda < 1 || nlambda > 65536) return fail(SKIRT_ERR_INVALID_ARG, "nlambda %d out of range", nlambda);
+    if (!is_device_ptr(emission)) return fail(SKIRT_ERR_INVALID_ARG, "emission must be device memory");
+    const std::vector<uint64_t> none((size_t)nlambda, 0);
+    std::vector<double> t;
+    if (int r = build_dust_cdf(g, emission, nlambda, none.data(), (cudaStream_t)stream, &t)) return r;
+    std::memcpy(totals, t.data(), sizeof(double) * (size_t)nlambda);
+    return SKIRT_OK;
+}
+
 extern "C" int skirt_grid_destroy(skirt_grid_t g)
 {
     if (!g) return SKIRT_OK;

@@ -220,8 +220,11 @@ __device__ double solve_T(int i, double ln_ratio)
     return exp(y);
 }
 
-// Exact emission for rows m = rows ? rows[k] : k, k < nrows.
+// Exact emission for rows m = rows ? rows[k] : k, k < nrows.  A second
+// absorbed table A2 [ncell][n2] with its shares w2 (may be NULL) adds its
+// power to each population's.
 __global__ void exact_kernel(const double* __restrict__ A, int n_in, const double* __restrict__ w,
+                             const double* __restrict__ A2, int n2, const double* __restrict__ w2,
                              const float* __restrict__ mass, const unsigned* __restrict__ rows,
                              long long nrows, double* __restrict__ emission, float* __restrict__ temperature)
 {
@@ -235,6 +238,15 @@ __global__ void exact_kernel(const double* __restrict__ A, int n_in, const doubl
             P[0] += __ldg(w + j) * a;
             P[1] += __ldg(w + n_in + j) * a;
             P[2] += __ldg(w + 2 * n_in + j) * a;
+        }
+        if (A2) {
+            const double* row2 = A2 + (size_t)m * n2;
+            for (int j = 0; j < n2; ++j) {
+                const double a = row2[j];
+                P[0] += __ldg(w2 + j) * a;
+                P[1] += __ldg(w2 + n2 + j) * a;
+                P[2] += __ldg(w2 + 2 * n2 + j) * a;
+            }
         }
         const double M = (double)mass[m];
         double T[NPOP], S[NPOP];
@@ -313,6 +325,7 @@ __device__ double solve_T_warp(int i, double ln_ratio, int lane)
 }
 
 __global__ void exact_warp_kernel(const double* __restrict__ A, int n_in, const double* __restrict__ w,
+                                  const double* __restrict__ A2, int n2, const double* __restrict__ w2,
                                   const float* __restrict__ mass, const unsigned* __restrict__ rows,
                                   long long nrows, double* __restrict__ emission, float* __restrict__ temperature)
 {
@@ -327,6 +340,15 @@ __global__ void exact_warp_kernel(const double* __restrict__ A, int n_in, const 
             p0 += __ldg(w + j) * a;
             p1 += __ldg(w + n_in + j) * a;
             p2 += __ldg(w + 2 * n_in + j) * a;
+        }
+        if (A2) {
+            const double* row2 = A2 + (size_t)m * n2;
+            for (int j = lane; j < n2; j += 32) {
+                const double a = row2[j];
+                p0 += __ldg(w2 + j) * a;
+                p1 += __ldg(w2 + n2 + j) * a;
+                p2 += __ldg(w2 + 2 * n2 + j) * a;
+            }
         }
         const double P[NPOP] = {warp_sum_bcast(p0), warp_sum_bcast(p1), warp_sum_bcast(p2)};
         const double M = (double)mass[m];
@@ -457,16 +479,16 @@ std::vector<double> share_table(const double* lam, int n)
 
 int launch_exact_emission(const double* absorbed, int n_in, const double* w_dev, const float* mass,
                           const unsigned* rows, long long nrows, double* emission, float* temperature,
-                          cudaStream_t s)
+                          cudaStream_t s, const double* absorbed2, int n2, const double* w2_dev)
 {
     ECK(upload_model(s));
     // a short row list: one warp per row keeps the Newton solves' latency short
     if (rows && nrows > 0 && nrows <= 8192)
-        exact_warp_kernel<<<(int)((nrows + 3) / 4), 128, 0, s>>>(absorbed, n_in, w_dev, mass, rows, nrows, emission,
-                                                                temperature);
+        exact_warp_kernel<<<(int)((nrows + 3) / 4), 128, 0, s>>>(absorbed, n_in, w_dev, absorbed2, n2, w2_dev, mass,
+                                                                rows, nrows, emission, temperature);
     else if (nrows > 0)
-        exact_kernel<<<grid_blocks(nrows, 128), 128, 0, s>>>(absorbed, n_in, w_dev, mass, rows, nrows, emission,
-                                                             temperature);
+        exact_kernel<<<grid_blocks(nrows, 128), 128, 0, s>>>(absorbed, n_in, w_dev, absorbed2, n2, w2_dev, mass, rows,
+                                                             nrows, emission, temperature);
     ECK(cudaGetLastError());
     return SKIRT_OK;
 }
@@ -602,6 +624,38 @@ extern "C" int skirt_dust_emission(const double* absorbed, long long ncell, int 
     return rc;
 }
 
+extern "C" int skirt_dust_emission_pair(const double* absorbed_a, long long ncell, int n_a, const double* lambda_a,
+                                        const double* absorbed_b, int n_b, const double* lambda_b, const float* mass,
+                                        double* emission, float* temperature, void* stream)
+{
+    if (ncell < 0) return set_error(SKIRT_ERR_INVALID_ARG, "ncell < 0");
+    if (int r = check_lambda(lambda_a, n_a)) return r;
+    if (absorbed_b || n_b) {
+        if (!absorbed_b) return set_error(SKIRT_ERR_INVALID_ARG, "absorbed_b is NULL with n_b > 0");
+        if (int r = check_lambda(lambda_b, n_b)) return r;
+    }
+    if (ncell == 0) return SKIRT_OK;
+    if (ncell >= (1ll << 32)) return set_error(SKIRT_ERR_INVALID_ARG, "ncell must be < 2^32");
+    if (!is_device(absorbed_a) || (absorbed_b && !is_device(absorbed_b)) || !is_device(mass) ||
+        !is_device(emission) || (temperature && !is_device(temperature)))
+        return set_error(SKIRT_ERR_INVALID_ARG, "absorbed / mass / emission / temperature must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<double> w = share_table(lambda_a, n_a);
+    if (absorbed_b) {
+        const std::vector<double> wb = share_table(lambda_b, n_b);
+        w.insert(w.end(), wb.begin(), wb.end());
+    }
+    double* d_w = nullptr;
+    ECK(cudaMallocAsync((void**)&d_w, sizeof(double) * w.size(), s));
+    ECK(cudaMemcpyAsync(d_w, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice, s));
+    int rc = launch_exact_emission(absorbed_a, n_a, d_w, mass, nullptr, ncell, emission, temperature, s, absorbed_b,
+                                   absorbed_b ? n_b : 0, absorbed_b ? d_w + (size_t)NPOP * n_a : nullptr);
+    cudaFreeAsync(d_w, s);
+    ECK(cudaStreamSynchronize(s));
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
 // Allocation-free exact emission.
 //

@@ -187,10 +187,12 @@ namespace skirt {
 // mlp.cu: tensor-core inference of the emission surrogate (stream-ordered, no sync)
 int mlp_forward_internal(skirt_mlp_s* net, const float* features, const double* total, long long n,
                          double* emission, unsigned char* flags, cudaStream_t s);
-// emission.cu: exact FP64 emission of rows (all rows when rows == NULL)
+// emission.cu: exact FP64 emission of rows (all rows when rows == NULL); a
+// second absorbed table [ncell][n2] with its shares (NULL: none) adds its power
 int launch_exact_emission(const double* absorbed, int n_in, const double* w_dev, const float* mass,
                           const unsigned* rows, long long nrows, double* emission, float* temperature,
-                          cudaStream_t s);
+                          cudaStream_t s, const double* absorbed2 = nullptr, int n2 = 0,
+                          const double* w2_dev = nullptr);
 // dust_source.cu: per-wavelength cumulative distribution of emission[cell][lambda]
 // over the cells, normalised to 1, into grid->cdf; the per-wavelength totals
 // into *totals_out (may be NULL).  INVALID_ARG when a wavelength with packets

@@ -310,10 +310,12 @@ def _bind_emission(L):
     L.skirt_mlp_forward.argtypes = [vp, vp, vp, ll, vp, vp, vp]
     L.skirt_dust_emission.argtypes = [vp, ll, i, _dp, vp, i, vp, vp, vp, ctypes.POINTER(skirt_emission_stats), vp]
     L.skirt_dust_emission_exact_static.argtypes = [vp, ll, i, _dp, vp, vp, vp, vp]
+    L.skirt_dust_emission_pair.argtypes = [vp, ll, i, _dp, vp, i, _dp, vp, vp, vp, vp]
+    L.skirt_emission_totals.argtypes = [vp, vp, i, _dp, vp]
     for name in ("skirt_emission_grid", "skirt_dust_mass", "skirt_band_features", "skirt_mlp_create",
                  "skirt_mlp_destroy", "skirt_mlp_set_params", "skirt_mlp_get_params", "skirt_mlp_train_opts_default",
                  "skirt_mlp_train", "skirt_mlp_grad", "skirt_mlp_forward", "skirt_dust_emission",
-                 "skirt_dust_emission_exact_static"):
+                 "skirt_dust_emission_exact_static", "skirt_dust_emission_pair", "skirt_emission_totals"):
         getattr(L, name).restype = i
 
 
@@ -352,6 +354,25 @@ def skirt_dust_emission(absorbed, ncell, n_in, lambda_in, mass, mode, net, emiss
                                    int(mode), None if net is None else net.h, _ptr(emission), _ptr(temperature),
                                    ctypes.byref(st), _st(stream)), "skirt_dust_emission")
     return st.as_dict()
+
+
+def skirt_emission_totals(grid, emission, nlambda, stream=None):
+    """Per-wavelength column sums (FP64, host) of a device emission table [ncell][nlambda]."""
+    t = np.zeros(int(nlambda))
+    _check(lib.skirt_emission_totals(grid, _ptr(emission), int(nlambda), t.ctypes.data_as(_dp), _st(stream)),
+           "skirt_emission_totals")
+    return t
+
+
+def skirt_dust_emission_pair(absorbed_a, ncell, lambda_a, absorbed_b, lambda_b, mass, emission, temperature=None,
+                             stream=None):
+    """Exact emission from two absorbed tables (absorbed_b / lambda_b may be None)."""
+    la = np.ascontiguousarray(lambda_a, dtype=np.float64)
+    lb = None if lambda_b is None else np.ascontiguousarray(lambda_b, dtype=np.float64)
+    _check(lib.skirt_dust_emission_pair(_ptr(absorbed_a), int(ncell), la.size, la.ctypes.data_as(_dp),
+                                        _ptr(absorbed_b), 0 if lb is None else lb.size,
+                                        None if lb is None else lb.ctypes.data_as(_dp), _ptr(mass), _ptr(emission),
+                                        _ptr(temperature), _st(stream)), "skirt_dust_emission_pair")
 
 
 def skirt_dust_emission_exact_static(absorbed, ncell, n_in, lambda_in, mass, emission, temperature=None, stream=None):
