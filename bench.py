@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--autotune", action="store_true")
-    ap.add_argument("--workload", default="disk", choices=["disk", "disk40", "torus", "learned"],
+    ap.add_argument("--workload", default="disk", choices=["disk", "disk40", "torus", "learned", "selfabs"],
                     help="disk: 1 wavelength, --packets packets (default); disk40: 40 wavelengths, "
                          "--packets per wavelength; torus: clumpy torus, 200 wavelengths, uneven counts "
                          "(--packets scales them, 1e8 = the full 7.5e8-packet run)")
@@ -280,6 +280,51 @@ def run_learned_report(args):
                       **rep}), flush=True)
 
 
+def run_selfabs_report(args):
+    """Dust self-absorption cycles on the clumpy torus (256^3, 200 stellar
+    wavelengths, then 1e6 dust packets per emission wavelength per cycle):
+    cycle count and per-stage times, as one JSON line (not the headline
+    metric)."""
+    import torch
+    from paper_1705_04702_gb300 import build
+    build.build()
+    from paper_1705_04702_gb300 import skirt as S
+    from paper_1705_04702_gb300 import workloads as W
+    from paper_1705_04702_gb300.selfabsorb import self_absorption
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    prob = W.torus_problem(n=args.grid, nlambda=200, npx=512, packet_scale=args.packets / 1e8)
+    grid = S.Grid(prob.grid)
+    ncell, NL = grid.ncell, prob.wl.n
+    absorbed = torch.zeros((ncell, NL), dtype=torch.float64, device="cuda")
+    opts = S.skirt_trace_opts_default()
+    opts.use_graph = 1
+    opts.peel = 0
+    tables = S.Tables(prob.wl)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, led, _ = S.skirt_trace(grid.h, S.make_source(prob.source), tables.c, prob.npk, prob.seed, [], opts, absorbed,
+                              None, None)
+    torch.cuda.synchronize()
+    t_star = time.perf_counter() - t0
+    mass = torch.empty(ncell, dtype=torch.float32, device="cuda")
+    S.skirt_dust_mass(grid.h, mass)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = self_absorption(grid, absorbed, prob.wl.lam, mass, 1_000_000, prob.seed, tol=1e-2, max_cycles=10)
+    torch.cuda.synchronize()
+    t_cycles = time.perf_counter() - t0
+    grid.close()
+    hist = [{"emitted": h["emitted"], "absorbed": h["absorbed"], "kernel_ms": h["ledger"]["kernel_ms"]}
+            for h in out["history"]]
+    print(json.dumps({"report": "dust self-absorption cycles",
+                      "workload": f"clumpy torus {args.grid}^3, 200 stellar wavelengths "
+                                  f"({prob.total_packets:.3e} packets, no peel-off), 100 dust wavelengths, "
+                                  f"1e6 dust packets per wavelength per cycle",
+                      "t_stellar_trace": t_star, "stellar_absorbed": led["absorbed"], "cycles": out["cycles"],
+                      "converged": out["converged"], "t_cycles": t_cycles, "t_per_cycle": t_cycles / out["cycles"],
+                      "history": hist}), flush=True)
+
+
 # ----------------------------------------------------------------------- ours
 def main():
     args = parse()
@@ -288,6 +333,9 @@ def main():
         return
     if args.workload == "learned":
         run_learned_report(args)
+        return
+    if args.workload == "selfabs":
+        run_selfabs_report(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
