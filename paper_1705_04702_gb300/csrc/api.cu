@@ -237,6 +237,8 @@ extern "C" int skirt_grid_destroy(skirt_grid_t g)
     g->scratch.release();
     g->stage.release();
     g->cdf.release();
+    g->cdf_aux.release();
+    g->abs_lmajor.release();
     g->pinned.release();
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
@@ -469,7 +471,24 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
     A.cdf = d_cdf;
     A.ninstr = peel ? ninstr : 0;
     A.ins = (const InstrDev*)(dp + L.ins);
-    A.absorbed = d_abs;
+    // With more than one wavelength the packets deposit into a wavelength-major
+    // table (consecutive cells of a wavelength adjacent, as the traversals
+    // visit them) and one transpose writes the [cell][lambda] result (the
+    // counterpart of the paper's column-to-row representation switch,
+    // Sect. 5.2); without room for that table they deposit in place.
+    bool lmajor = NL > 1;
+    double* d_acc = d_abs;
+    if (lmajor) {
+        if (g->abs_lmajor.ensure(abs_bytes) == cudaSuccess) {
+            d_acc = (double*)g->abs_lmajor.p;
+        } else {
+            cudaGetLastError();
+            lmajor = false;
+        }
+    }
+    A.absorbed = d_acc;
+    A.abs_cs = lmajor ? 1 : NL;
+    A.abs_ls = lmajor ? g->ncell : 1;
     A.images = d_img;
     A.oof = (double*)(dp + L.oof);
     A.ledger = (double*)(dp + L.ledger);
@@ -500,8 +519,9 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
 
     // ---- the device work of one call (recorded into a graph when asked)
     auto enqueue = [&](cudaStream_t s, bool events) -> int {
+        if (lmajor) CK(cudaMemsetAsync(d_acc, 0, abs_bytes, s));
         if (!opts->accumulate) {
-            CK(cudaMemsetAsync(d_abs, 0, abs_bytes, s));
+            if (!lmajor) CK(cudaMemsetAsync(d_abs, 0, abs_bytes, s));
             if (peel) {
                 CK(cudaMemsetAsync(d_img, 0, img_bytes, s));
                 CK(cudaMemsetAsync(d_sed, 0, sed_bytes, s));
@@ -531,6 +551,7 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
             }
         }
         CK(events ? cudaEventRecord(g->ev1, s) : cudaEventRecordWithFlags(g->ev1, s, cudaEventRecordExternal));
+        if (lmajor) CK(launch_transpose_absorbed(d_acc, d_abs, g->ncell, NL, opts->accumulate != 0, s));
         if (peel) CK(launch_sed_finalize(d_img, A.oof, d_sed, ninstr, P.npx.data(), NL, 1.0, s));
         return SKIRT_OK;
     };

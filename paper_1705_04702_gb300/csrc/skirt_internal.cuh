@@ -72,7 +72,8 @@ struct TraceArgs {
     const double* cdf;                     // dust source: [nlambda][ncell] cumulative, normalised
     int ninstr;
     const InstrDev* ins;
-    double* absorbed;                      // [ncell][nlambda]
+    double* absorbed;                      // element (cell, lambda) at cell * abs_cs + lambda * abs_ls
+    long long abs_cs, abs_ls;              // [cell][lambda]: (nlambda, 1); [lambda][cell]: (1, ncell)
     double* images;                        // per instrument [npx*npx][nlambda]
     double* oof;                           // [ninstr][nlambda] peel-offs outside the frame
     double* ledger;                        // [nlambda][4]
@@ -100,6 +101,10 @@ size_t trace_smem_bytes(int ninstr, int block);
 cudaError_t launch_trace_mixed(const TraceArgs& a, int block, int grid, cudaStream_t s);
 cudaError_t trace_mixed_occupancy(int block, int* blocks_per_sm);
 size_t trace_mixed_smem_bytes(int ninstr, int block);
+// out[cell][lambda] (+)= in[lambda][cell]: the absorbed table from the trace's
+// wavelength-major accumulation to the API's cell-major layout
+cudaError_t launch_transpose_absorbed(const double* in, double* out, long long ncell, int nlambda, bool add,
+                                      cudaStream_t s);
 // sed[q][lambda] += sign * (sum over the pixels of images_q) + oof[q][lambda] (oof may be NULL)
 cudaError_t launch_sed_finalize(const double* images, const double* oof, double* sed, int ninstr,
                                 const int* npx_host, int nlambda, double sign, cudaStream_t s);
@@ -174,6 +179,7 @@ struct skirt_grid_s {
     skirt::DevBuf stage;    // device images of host outputs
     skirt::DevBuf cdf;      // dust source: [nlambda][ncell] cumulative distributions
     skirt::DevBuf cdf_aux;  // dust source: tile sums and totals
+    skirt::DevBuf abs_lmajor;  // wavelength-major absorbed table of the current call
     skirt::PinnedBuf pinned;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaStream_t capture_stream = nullptr;

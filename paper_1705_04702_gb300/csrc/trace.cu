@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A)
                 if (dtau_r > (R)0) {
                     const double dep = labs * P<R>::dep_factor(tau, dtau_r);
                     if (dep > 0.0) {
-                        atomicAdd(A.absorbed + (size_t)m * NL + lam, dep);
+                        atomicAdd(A.absorbed + ((size_t)m * A.abs_cs + (size_t)lam * A.abs_ls), dep);
                         p_abs += dep;
                     }
                 }
@@ -491,6 +491,44 @@ cudaError_t trace_occupancy(int precision, int block, int* blocks_per_sm)
     if (precision == SKIRT_PREC_MIXED) return trace_mixed_occupancy(block, blocks_per_sm);
     const size_t smem = trace_smem_bytes(16, block);
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<double>, block, smem);
+}
+
+namespace {
+
+// out[c][l] (+)= in[l][c], 32 x 32 tiles through shared memory (one padding
+// column): coalesced reads along the cells and writes along the wavelengths.
+__global__ void transpose_absorbed_kernel(const double* __restrict__ in, double* __restrict__ out, long long ncell,
+                                          int nl, int add)
+{
+    __shared__ double tile[32][33];
+    const long long c0 = (long long)blockIdx.x * 32;
+    const int l0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const long long c = c0 + threadIdx.x;
+        const int l = l0 + k;
+        tile[k][threadIdx.x] = (c < ncell && l < nl) ? in[(size_t)l * ncell + c] : 0.0;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const long long c = c0 + k;
+        const int l = l0 + threadIdx.x;
+        if (c < ncell && l < nl) {
+            double* o = out + (size_t)c * nl + l;
+            *o = add ? *o + tile[threadIdx.x][k] : tile[threadIdx.x][k];
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_transpose_absorbed(const double* in, double* out, long long ncell, int nlambda, bool add,
+                                      cudaStream_t s)
+{
+    const long long bx = (ncell + 31) / 32;
+    if (bx > 0x7fffffffLL) return cudaErrorInvalidValue;
+    transpose_absorbed_kernel<<<dim3((unsigned)bx, (unsigned)((nlambda + 31) / 32)), dim3(32, 8), 0, s>>>(
+        in, out, ncell, nlambda, add ? 1 : 0);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sed_finalize(const double* images, const double* oof, double* sed, int ninstr,

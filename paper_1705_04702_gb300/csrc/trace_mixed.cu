@@ -254,7 +254,8 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
             }
         } else if (mode == M_DEPOSIT && dtau > 0.f) {
             const float dep = labs_f * exp_neg(tau_prev) * one_minus_exp_neg(dtau);
-            if (dep >= 1.17549435e-38f) atomicAdd(absorbed + (size_t)m * NL + lam, f2d_pos(dep));
+            if (dep >= 1.17549435e-38f)
+                atomicAdd(absorbed + ((size_t)m * A.abs_cs + (size_t)lam * A.abs_ls), f2d_pos(dep));
         }
         df_accumulate(tau_h, tau_l, dtau);
         if (!done) {
