@@ -37,10 +37,16 @@ __constant__ double c_lnc[NPOP];        // ln c_i = -ln G_i(30 K)
 __constant__ double c_lnG_lo[NPOP];     // ln G_i(3 K)
 __constant__ double c_lnG_hi[NPOP];     // ln G_i(2000 K)
 __constant__ double c_beta[NPOP];
+// ln G_i and d ln G_i / d ln T at NTAB log-spaced temperatures over [T_LO,
+// T_HI]: the starting point of the Newton solve (read through the L1 path)
+constexpr int NTAB = 128;
+__device__ double g_lnG_tab[NPOP][NTAB];
+__device__ double g_dlnG_tab[NPOP][NTAB];
 
 struct HostModel {
     double lam[NOUT], W[NOUT], a[NOUT], K[NPOP][NOUT];
     double lnc[NPOP], lnG_lo[NPOP], lnG_hi[NPOP];
+    double tab[NPOP][NTAB], dtab[NPOP][NTAB];
 };
 
 double host_G(const HostModel& h, int i, double T)
@@ -69,6 +75,19 @@ const HostModel& host_model()
             h.lnc[i] = -std::log(host_G(h, i, T_REF));
             h.lnG_lo[i] = std::log(host_G(h, i, T_LO));
             h.lnG_hi[i] = std::log(host_G(h, i, T_HI));
+            for (int k = 0; k < NTAB; ++k) {
+                const double T = std::exp(std::log(T_LO) + (std::log(T_HI) - std::log(T_LO)) * k / (NTAB - 1));
+                double g = 0.0, d = 0.0;
+                for (int l = 0; l < NOUT; ++l) {
+                    const double x = h.a[l] / T;
+                    if (x > 700.0) continue;
+                    const double q = 1.0 / std::expm1(x);
+                    g += h.K[i][l] * q;
+                    d += h.K[i][l] * q * x * (1.0 + q);
+                }
+                h.tab[i][k] = std::log(g);
+                h.dtab[i][k] = d / g;
+            }
         }
         ready = true;
     }
@@ -84,6 +103,8 @@ cudaError_t upload_model(cudaStream_t s)
     if ((e = cudaMemcpyToSymbolAsync(c_lnc, h.lnc, sizeof h.lnc, 0, cudaMemcpyHostToDevice, s))) return e;
     if ((e = cudaMemcpyToSymbolAsync(c_lnG_lo, h.lnG_lo, sizeof h.lnG_lo, 0, cudaMemcpyHostToDevice, s))) return e;
     if ((e = cudaMemcpyToSymbolAsync(c_lnG_hi, h.lnG_hi, sizeof h.lnG_hi, 0, cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyToSymbolAsync(g_lnG_tab, h.tab, sizeof h.tab, 0, cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyToSymbolAsync(g_dlnG_tab, h.dtab, sizeof h.dtab, 0, cudaMemcpyHostToDevice, s))) return e;
     return cudaMemcpyToSymbolAsync(c_beta, BETA, sizeof BETA, 0, cudaMemcpyHostToDevice, s);
 }
 
@@ -183,12 +204,15 @@ int band_blocks(long long ncell)
 }
 
 // G_i(T) = sum_l K_il / expm1(a_l / T) and T dG/dT = sum K_il q x (1 + q)
+// (x_l = a_l / T is formed as a_l (1/T): one division per evaluation; the
+// output rows use the same K_il q_l products, so they sum to the power exactly)
 __device__ void pop_G(int i, double T, double& G, double& D)
 {
     G = 0.0;
     D = 0.0;
+    const double invT = 1.0 / T;
     for (int l = 0; l < NOUT; ++l) {
-        const double x = c_a[l] / T;
+        const double x = c_a[l] * invT;
         if (x > 700.0) continue;  // e^x overflows; the term is below 1e-300 of the largest
         const double q = 1.0 / expm1(x);
         const double t = c_K[i][l] * q;
@@ -197,27 +221,63 @@ __device__ void pop_G(int i, double T, double& G, double& D)
     }
 }
 
-__device__ double solve_T(int i, double ln_ratio)
+// Starting point and bracket of the Newton solve for ln G_i(e^y) = target:
+// the table interval holding the target, and the cubic Hermite inverse of
+// ln G on it (slopes dy/d lnG = 1 / (d lnG / dy)), a few 1e-8 from the root.
+__device__ __forceinline__ void start_T(int i, double target, double& y, double& lo, double& hi)
+{
+    const double* tab = &g_lnG_tab[i][0];
+    int a = 0, b = NTAB - 1;  // tab[a] <= target < tab[b]
+    while (b - a > 1) {
+        const int mid = (a + b) >> 1;
+        if (__ldg(tab + mid) <= target) a = mid; else b = mid;
+    }
+    const double dy = (log(T_HI) - log(T_LO)) / (NTAB - 1);
+    lo = log(T_LO) + a * dy;
+    hi = lo + dy;
+    const double ga = __ldg(tab + a), gb = __ldg(tab + b);
+    const double h = gb - ga, u = (target - ga) / h;
+    const double sa = 1.0 / __ldg(&g_dlnG_tab[i][a]), sb = 1.0 / __ldg(&g_dlnG_tab[i][b]);
+    const double u2 = u * u, u3 = u2 * u;
+    y = (2.0 * u3 - 3.0 * u2 + 1.0) * lo + (u3 - 2.0 * u2 + u) * h * sa + (3.0 * u2 - 2.0 * u3) * hi +
+        (u3 - u2) * h * sb;
+    if (!(y > lo && y < hi)) y = 0.5 * (lo + hi);
+}
+
+// T_i solving c_i G_i(T) = P_i / M (ln_ratio = ln(P_i / M)) by Newton on
+// ln T from the table start, bisection inside the bracket when a step leaves
+// it; clamped to [T_LO, T_HI].  G_out receives G_i at the returned T (the
+// point of the last evaluation, whose Newton step was below 1e-13 relative),
+// so that emission rows normalised by it sum to P_i exactly.
+__device__ double solve_T(int i, double ln_ratio, double& G_out)
 {
     const double target = ln_ratio - c_lnc[i];  // ln G at the solution
-    if (c_lnG_lo[i] - target >= 0.0) return T_LO;
-    if (c_lnG_hi[i] - target <= 0.0) return T_HI;
-    double lo = log(T_LO), hi = log(T_HI);
-    // G ~ T^(4+beta) on the Rayleigh-Jeans side of the grid: first guess
-    double y = log(T_REF) + ln_ratio / (4.0 + c_beta[i]);
-    if (!(y > lo && y < hi)) y = 0.5 * (lo + hi);
+    double G, D;
+    if (c_lnG_lo[i] - target >= 0.0 || c_lnG_hi[i] - target <= 0.0) {
+        const double T = c_lnG_lo[i] - target >= 0.0 ? T_LO : T_HI;
+        pop_G(i, T, G, D);
+        G_out = G;
+        return T;
+    }
+    double y, lo, hi;
+    start_T(i, target, y, lo, hi);
     for (int it = 0; it < 100; ++it) {
-        double G, D;
-        pop_G(i, exp(y), G, D);
+        const double T = exp(y);
+        pop_G(i, T, G, D);
         const double f = log(G) - target;
         if (f < 0.0) lo = y; else hi = y;
         double y_new = y - f * G / D;
         if (!(y_new > lo && y_new < hi)) y_new = 0.5 * (lo + hi);
-        const bool done = fabs(y_new - y) <= 1e-13 * fabs(y);
+        if (fabs(y_new - y) <= 1e-13 * fabs(y)) {
+            G_out = G;
+            return T;
+        }
         y = y_new;
-        if (done) break;
     }
-    return exp(y);
+    const double T = exp(y);
+    pop_G(i, T, G, D);
+    G_out = G;
+    return T;
 }
 
 // Exact emission for rows m = rows ? rows[k] : k, k < nrows.  A second
@@ -253,20 +313,20 @@ __global__ void exact_kernel(const double* __restrict__ A, int n_in, const doubl
         for (int i = 0; i < NPOP; ++i) {
             T[i] = 0.0;
             S[i] = 0.0;
-            if (P[i] > 0.0 && M > 0.0) {
-                T[i] = solve_T(i, log(P[i] / M));
-                double G, D;
-                pop_G(i, T[i], G, D);
-                S[i] = G;
-            }
+            if (P[i] > 0.0 && M > 0.0) T[i] = solve_T(i, log(P[i] / M), S[i]);
         }
         double* out = emission + (size_t)m * NOUT;
+        double invT[NPOP], PS[NPOP];
+        for (int i = 0; i < NPOP; ++i) {
+            invT[i] = S[i] > 0.0 ? 1.0 / T[i] : 0.0;
+            PS[i] = S[i] > 0.0 ? P[i] / S[i] : 0.0;
+        }
         for (int l = 0; l < NOUT; ++l) {
             double e = 0.0;
             for (int i = 0; i < NPOP; ++i) {
                 if (S[i] > 0.0) {
-                    const double x = c_a[l] / T[i];
-                    if (x <= 700.0) e += P[i] * (c_K[i][l] / expm1(x)) / S[i];
+                    const double x = c_a[l] * invT[i];
+                    if (x <= 700.0) e += PS[i] * (c_K[i][l] * (1.0 / expm1(x)));
                 }
             }
             out[l] = e;
@@ -290,8 +350,9 @@ __device__ __forceinline__ double warp_sum_bcast(double v)
 __device__ void pop_G_warp(int i, double T, double& G, double& D, int lane)
 {
     double g = 0.0, d = 0.0;
+    const double invT = 1.0 / T;
     for (int l = lane; l < NOUT; l += 32) {
-        const double x = c_a[l] / T;
+        const double x = c_a[l] * invT;
         if (x > 700.0) continue;
         const double q = 1.0 / expm1(x);
         const double t = c_K[i][l] * q;
@@ -302,26 +363,35 @@ __device__ void pop_G_warp(int i, double T, double& G, double& D, int lane)
     D = warp_sum_bcast(d);
 }
 
-__device__ double solve_T_warp(int i, double ln_ratio, int lane)
+__device__ double solve_T_warp(int i, double ln_ratio, int lane, double& G_out)
 {
     const double target = ln_ratio - c_lnc[i];
-    if (c_lnG_lo[i] - target >= 0.0) return T_LO;
-    if (c_lnG_hi[i] - target <= 0.0) return T_HI;
-    double lo = log(T_LO), hi = log(T_HI);
-    double y = log(T_REF) + ln_ratio / (4.0 + c_beta[i]);
-    if (!(y > lo && y < hi)) y = 0.5 * (lo + hi);
+    double G, D;
+    if (c_lnG_lo[i] - target >= 0.0 || c_lnG_hi[i] - target <= 0.0) {
+        const double T = c_lnG_lo[i] - target >= 0.0 ? T_LO : T_HI;
+        pop_G_warp(i, T, G, D, lane);
+        G_out = G;
+        return T;
+    }
+    double y, lo, hi;
+    start_T(i, target, y, lo, hi);
     for (int it = 0; it < 100; ++it) {
-        double G, D;
-        pop_G_warp(i, exp(y), G, D, lane);
+        const double T = exp(y);
+        pop_G_warp(i, T, G, D, lane);
         const double f = log(G) - target;
         if (f < 0.0) lo = y; else hi = y;
         double y_new = y - f * G / D;
         if (!(y_new > lo && y_new < hi)) y_new = 0.5 * (lo + hi);
-        const bool done = fabs(y_new - y) <= 1e-13 * fabs(y);
+        if (fabs(y_new - y) <= 1e-13 * fabs(y)) {
+            G_out = G;
+            return T;
+        }
         y = y_new;
-        if (done) break;
     }
-    return exp(y);
+    const double T = exp(y);
+    pop_G_warp(i, T, G, D, lane);
+    G_out = G;
+    return T;
 }
 
 __global__ void exact_warp_kernel(const double* __restrict__ A, int n_in, const double* __restrict__ w,
@@ -357,21 +427,22 @@ __global__ void exact_warp_kernel(const double* __restrict__ A, int n_in, const 
         for (int i = 0; i < NPOP; ++i) {
             T[i] = 0.0;
             S[i] = 0.0;
-            if (P[i] > 0.0 && M > 0.0) {
-                T[i] = solve_T_warp(i, log(P[i] / M), lane);
-                double G, D;
-                pop_G_warp(i, T[i], G, D, lane);
-                S[i] = G;
-            }
+            if (P[i] > 0.0 && M > 0.0) T[i] = solve_T_warp(i, log(P[i] / M), lane, S[i]);
         }
         double* out = emission + (size_t)m * NOUT;
+        double invT[NPOP], PS[NPOP];
+#pragma unroll
+        for (int i = 0; i < NPOP; ++i) {
+            invT[i] = S[i] > 0.0 ? 1.0 / T[i] : 0.0;
+            PS[i] = S[i] > 0.0 ? P[i] / S[i] : 0.0;
+        }
         for (int l = lane; l < NOUT; l += 32) {
             double e = 0.0;
 #pragma unroll
             for (int i = 0; i < NPOP; ++i) {
                 if (S[i] > 0.0) {
-                    const double x = c_a[l] / T[i];
-                    if (x <= 700.0) e += P[i] * (c_K[i][l] / expm1(x)) / S[i];
+                    const double x = c_a[l] * invT[i];
+                    if (x <= 700.0) e += PS[i] * (c_K[i][l] * (1.0 / expm1(x)));
                 }
             }
             out[l] = e;
