@@ -44,7 +44,7 @@ namespace {
 
 constexpr int MAXB = 256;       // threads per block of the mixed kernel (upper bound)
 constexpr int ROUND = 8;        // cell crossings per stepping round between warp votes
-constexpr float TAU_CUT = 50.f; // optical depth after which a deposit / peel-off traversal stops
+constexpr float TAU_CUT = 30.f; // optical depth after which a deposit / peel-off traversal stops
 
 // FP32 -> FP64 by IEEE-754 field manipulation on the integer pipe: exact for
 // normal floats; zero and FP32 subnormals map to zero.
@@ -279,10 +279,11 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                 last_axis = axis;
             }
         }
-        // Beyond tau = TAU_CUT a line of sight transmits < e^-50 and a deposit
-        // path has handed < e^-50 of the luminosity to its remaining cells:
-        // the traversal ends there (the search never gets that far, since
-        // tau_int < 17 in FP32).
+        // Beyond tau = TAU_CUT a line of sight transmits < e^-30 (1e-13) and a
+        // deposit path has handed < e^-30 of the luminosity to its remaining
+        // cells; 1 - e^-tau is 1 in FP32 from tau = 17 on, so the forced
+        // scattering draw does not change: the traversal ends there (the search
+        // never gets that far, since tau_int < 17 in FP32).
         if (tau_h > TAU_CUT && mode != M_LOCATE) done = true;
         if (done) mode = M_NONE;
     };
