@@ -382,9 +382,14 @@ __global__ void colsum_kernel(const float* d, float* out, int rows, int cols)
     if (threadIdx.x == 0) out[c] = red[0];
 }
 
-__global__ void adam_kernel(float* p, const float* g, float* m, float* v, int n, float lr, float b1, float b2,
-                            float eps, float c1, float c2)
+// Adam with this step's learning rate and bias corrections read from the
+// schedule (sched[3t..3t+2] = lr, 1 - b1^(t+1), 1 - b2^(t+1)) at the device
+// step counter t, so that one captured graph serves every step
+__global__ void adam_sched_kernel(float* p, const float* g, float* m, float* v, int n, const float* __restrict__ sched,
+                                  const long long* __restrict__ t_dev, float b1, float b2, float eps)
 {
+    const long long t = *t_dev;
+    const float lr = sched[3 * t], c1 = sched[3 * t + 1], c2 = sched[3 * t + 2];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float gi = g[i];
         const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -395,11 +400,16 @@ __global__ void adam_kernel(float* p, const float* g, float* m, float* v, int n,
     }
 }
 
-// batch gather with an affine permutation of the sample indices, standardising the features
-__global__ void gather_kernel(const float* __restrict__ feat, const float* __restrict__ target, long long n,
-                              long long first, unsigned long long a, unsigned long long b, int rows,
-                              const float* __restrict__ stats, float* __restrict__ xb, float* __restrict__ tb)
+// the batch of step t: sample r of the batch is (a (k B + r) + b) mod n with
+// k = t mod steps and (a, b) the permutation of epoch t / steps
+__global__ void gather_sched_kernel(const float* __restrict__ feat, const float* __restrict__ target, long long n,
+                                    const unsigned long long* __restrict__ ab, const long long* __restrict__ t_dev,
+                                    long long steps, int rows, const float* __restrict__ stats, float* __restrict__ xb,
+                                    float* __restrict__ tb)
 {
+    const long long t = *t_dev;
+    const unsigned long long a = ab[2 * (t / steps)], b = ab[2 * (t / steps) + 1];
+    const long long first = (t % steps) * rows;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows * (NIN + NO); i += gridDim.x * blockDim.x) {
         const int r = i / (NIN + NO), c = i % (NIN + NO);
         const unsigned long long src = (a * (unsigned long long)(first + r) + b) % (unsigned long long)n;
@@ -407,6 +417,8 @@ __global__ void gather_kernel(const float* __restrict__ feat, const float* __res
         else tb[(size_t)r * NO + (c - NIN)] = target[src * NO + (c - NIN)];
     }
 }
+
+__global__ void step_advance_kernel(long long* t_dev) { *t_dev += 1; }
 
 // out[r][c] = in[r][c] / sum_c in[r][c] in FP32 (one warp per row; zero rows stay zero)
 __global__ void normalize_rows_kernel(const double* __restrict__ in, float* __restrict__ out, long long rows)
@@ -797,36 +809,88 @@ extern "C" int skirt_mlp_train(skirt_mlp_t net, const float* features, const dou
     MCK(w.alloc(B, s));
     const long long steps = n / B;
     const long long total_steps = steps * opts->epochs;
+    // per-epoch permutations (affine i -> (a i + b) mod n with a coprime to n)
+    // and the per-step schedule (cosine learning rate, Adam bias corrections),
+    // computed on the host and read on the device at the step counter
+    std::vector<unsigned long long> ab(2 * (size_t)opts->epochs);
+    std::vector<float> sched(3 * (size_t)total_steps);
     uint64_t rs = opts->seed ^ 0x5DEECE66Dull;
-    long long t = 0;
+    auto gcd = [](unsigned long long x, unsigned long long y) {
+        while (y) { unsigned long long r = x % y; x = y; y = r; }
+        return x;
+    };
     for (int ep = 0; ep < opts->epochs; ++ep) {
-        // affine permutation i -> (a i + b) mod n with a coprime to n
         unsigned long long a = (splitmix64(rs) % (unsigned long long)n) | 1ull;
-        auto gcd = [](unsigned long long x, unsigned long long y) {
-            while (y) { unsigned long long r = x % y; x = y; y = r; }
-            return x;
-        };
         while (gcd(a, (unsigned long long)n) != 1) a += 2;
-        const unsigned long long b = splitmix64(rs) % (unsigned long long)n;
-        MCK(cudaMemsetAsync(w.loss, 0, sizeof(float), s));
-        for (long long k = 0; k < steps; ++k, ++t) {
-            gather_kernel<<<blocks_for((long long)B * (NIN + NO), 256), 256, 0, s>>>(features, target, n, k * B, a, b,
-                                                                                    B, net->stats, w.xb, w.tb);
-            fwd_bwd(net, w, B, s);
-            const double frac = (double)t / (double)(total_steps > 1 ? total_steps - 1 : 1);
-            const float lr = (float)(opts->lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(M_PI * frac))));
-            const float c1 = 1.f - std::pow(opts->beta1, (float)(t + 1));
-            const float c2 = 1.f - std::pow(opts->beta2, (float)(t + 1));
-            adam_kernel<<<blocks_for(NPARAM, 256), 256, 0, s>>>(net->P, net->G, net->Mo, net->Vo, NPARAM, lr,
-                                                                opts->beta1, opts->beta2, opts->eps, c1, c2);
-        }
-        MCK(cudaGetLastError());
-        if (loss_history) {
+        ab[2 * ep] = a;
+        ab[2 * ep + 1] = splitmix64(rs) % (unsigned long long)n;
+    }
+    for (long long t = 0; t < total_steps; ++t) {
+        const double frac = (double)t / (double)(total_steps > 1 ? total_steps - 1 : 1);
+        sched[3 * t] = (float)(opts->lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(M_PI * frac))));
+        sched[3 * t + 1] = 1.f - std::pow(opts->beta1, (float)(t + 1));
+        sched[3 * t + 2] = 1.f - std::pow(opts->beta2, (float)(t + 1));
+    }
+    unsigned long long* d_ab = nullptr;
+    float* d_sched = nullptr;
+    long long* d_t = nullptr;
+    MCK(cudaMallocAsync((void**)&d_ab, sizeof(unsigned long long) * ab.size(), s));
+    MCK(cudaMallocAsync((void**)&d_sched, sizeof(float) * sched.size(), s));
+    MCK(cudaMallocAsync((void**)&d_t, sizeof(long long), s));
+    MCK(cudaMemcpyAsync(d_ab, ab.data(), sizeof(unsigned long long) * ab.size(), cudaMemcpyHostToDevice, s));
+    MCK(cudaMemcpyAsync(d_sched, sched.data(), sizeof(float) * sched.size(), cudaMemcpyHostToDevice, s));
+    MCK(cudaMemsetAsync(d_t, 0, sizeof(long long), s));
+
+    // one training step (gather, forward, backward, Adam, step counter) as a
+    // CUDA graph, captured on a private stream and replayed for every step
+    cudaStream_t cs = nullptr;
+    MCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaEvent_t ready = nullptr;
+    MCK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    MCK(cudaEventRecord(ready, s));
+    MCK(cudaStreamWaitEvent(cs, ready, 0));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int rc = SKIRT_OK;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        gather_sched_kernel<<<blocks_for((long long)B * (NIN + NO), 256), 256, 0, cs>>>(features, target, n, d_ab, d_t,
+                                                                                       steps, B, net->stats, w.xb,
+                                                                                       w.tb);
+        fwd_bwd(net, w, B, cs);
+        adam_sched_kernel<<<blocks_for(NPARAM, 256), 256, 0, cs>>>(net->P, net->G, net->Mo, net->Vo, NPARAM, d_sched,
+                                                                  d_t, opts->beta1, opts->beta2, opts->eps);
+        step_advance_kernel<<<1, 1, 0, cs>>>(d_t);
+        e = cudaStreamEndCapture(cs, &graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
+    if (e != cudaSuccess) rc = set_error(SKIRT_ERR_CUDA, "training graph: %s", cudaGetErrorString(e));
+    for (int ep = 0; ep < opts->epochs && rc == SKIRT_OK; ++ep) {
+        e = cudaMemsetAsync(w.loss, 0, sizeof(float), cs);
+        for (long long k = 0; k < steps && e == cudaSuccess; ++k) e = cudaGraphLaunch(gexec, cs);
+        if (e == cudaSuccess && loss_history) {
             float l = 0.f;
-            MCK(cudaMemcpyAsync(&l, w.loss, sizeof(float), cudaMemcpyDeviceToHost, s));
-            MCK(cudaStreamSynchronize(s));
+            e = cudaMemcpyAsync(&l, w.loss, sizeof(float), cudaMemcpyDeviceToHost, cs);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
             loss_history[ep] = l / (float)steps;
         }
+        if (e != cudaSuccess) rc = set_error(SKIRT_ERR_CUDA, "training step: %s", cudaGetErrorString(e));
+    }
+    cudaEventRecord(ready, cs);
+    cudaStreamWaitEvent(s, ready, 0);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamSynchronize(cs);
+    cudaStreamDestroy(cs);
+    cudaEventDestroy(ready);
+    cudaFreeAsync(d_ab, s);
+    cudaFreeAsync(d_sched, s);
+    cudaFreeAsync(d_t, s);
+    if (rc) {
+        w.release(s);
+        cudaFreeAsync(target, s);
+        cudaStreamSynchronize(s);
+        return rc;
     }
     w.release(s);
     cudaFreeAsync(target, s);
