@@ -676,6 +676,7 @@ extern "C" int skirt_dust_emission(const double* absorbed, long long ncell, int 
     }
     cudaFreeAsync(d_w, s);
     ECK(cudaStreamSynchronize(s));
+    if (rc == SKIRT_OK && mode == SKIRT_EMIT_SURROGATE) rc = mlp_check_timeout();
     if (stats && rc == SKIRT_OK) {
         stats->n_cells = (unsigned long long)ncell;
         stats->n_fallback = nfb;

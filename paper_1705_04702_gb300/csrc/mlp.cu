@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <vector>
 
@@ -53,16 +54,65 @@ constexpr int INF_ROWS = 16 * INF_WARPS;
 // every row padded by 8 elements, so that the eight rows one fragment load
 // touches start 4 banks apart (conflict-free); biases [128 + 128 + 104]
 // (fp32); mean / inv_std / lo / hi [32] each; per-warp feature staging
-// [16][33] fp32 (one padding column, conflict-free column reads)
-constexpr int KP1 = NIN + 8, KP2 = NH + 8, XP = NIN + 1;
+constexpr int KP1 = NIN + 8, KP2 = NH + 8;
 constexpr size_t SM_W1 = 0;
 constexpr size_t SM_W2 = SM_W1 + sizeof(uint16_t) * NH * KP1;
 constexpr size_t SM_W3 = SM_W2 + sizeof(uint16_t) * NH * KP2;
 constexpr size_t SM_B = SM_W3 + sizeof(uint16_t) * NO_PAD * KP2;
 constexpr size_t SM_ST = SM_B + sizeof(float) * (NH + NH + NO_PAD);
-constexpr size_t SM_X = SM_ST + sizeof(float) * 4 * NIN;
-constexpr size_t SM_TOTAL = SM_X + sizeof(float) * INF_WARPS * 16 * XP;
+// per warp: two 16-row feature tiles [16][32] fp32 that the bulk copy engine
+// fills asynchronously (128-byte aligned), and their two mbarriers
+constexpr size_t SM_X = (SM_ST + sizeof(float) * 4 * NIN + 127) & ~(size_t)127;
+constexpr size_t SM_BAR = SM_X + sizeof(float) * INF_WARPS * 2 * 16 * NIN;
+constexpr size_t SM_TOTAL = SM_BAR + sizeof(unsigned long long) * INF_WARPS * 2;
 static_assert((KP1 * 2) % 16 == 0 && (KP2 * 2) % 16 == 0, "padded rows keep 16-byte alignment");
+
+// Bulk asynchronous copies (global -> shared) completing on an mbarrier, in
+// inline PTX.  Waits are bounded: a wait that runs out sets g_mlp_timeout and
+// the kernel stops instead of spinning on.
+__device__ unsigned g_mlp_timeout;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// orders this thread's earlier generic accesses to shared memory before later
+// asynchronous-proxy writes (the next bulk copy into a buffer just read)
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity)
+{
+    const unsigned a = smem_u32(bar);
+    for (int i = 0; i < (1 << 20); ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
@@ -166,33 +216,52 @@ __global__ void __launch_bounds__(32 * INF_WARPS, 2) mlp_infer_kernel(
     const float* hhi = hlo + NIN;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, t = lane & 3;
-    float* xs = reinterpret_cast<float*>(sm + SM_X) + warp * 16 * XP;
-
-    for (long long base = (long long)blockIdx.x * INF_ROWS + warp * 16; base < n;
-         base += (long long)gridDim.x * INF_ROWS) {
-        // ---- features of 16 rows: coalesced load, hull check, standardise
-        for (int i = lane; i < 16 * NIN; i += 32) {
-            const long long r = base + i / NIN;
-            xs[(i / NIN) * XP + (i % NIN)] = r < n ? features[r * NIN + (i % NIN)] : 0.f;
+    float* xbuf = reinterpret_cast<float*>(sm + SM_X) + warp * 2 * 16 * NIN;  // [2][16][32]
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm + SM_BAR) + warp * 2;
+    if (lane == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_barrier_init();
+    }
+    __syncwarp();
+    const long long stride = (long long)gridDim.x * INF_ROWS;
+    // the 16 feature rows of the tile at row b (fewer at the end), 128 bytes each
+    auto fetch = [&](long long b, int buf) {
+        const long long rows = n - b < 16 ? n - b : 16;
+        fence_proxy_async();
+        bulk_load(xbuf + buf * 16 * NIN, features + b * NIN, (unsigned)(rows * NIN * sizeof(float)), &bar[buf]);
+    };
+    long long base = (long long)blockIdx.x * INF_ROWS + warp * 16;
+    if (lane == 0 && base < n) fetch(base, 0);
+    for (long long k = 0; base < n; base += stride, ++k) {
+        const int buf = (int)(k & 1);
+        // the next tile streams in while this one is computed
+        if (lane == 0 && base + stride < n) fetch(base + stride, buf ^ 1);
+        if (!mbar_wait(&bar[buf], (unsigned)((k >> 1) & 1))) {
+            atomicOr(&g_mlp_timeout, 1u);
+            if (lane == 0 && base + stride < n) mbar_wait(&bar[buf ^ 1], (unsigned)(((k + 1) >> 1) & 1));
+            break;
         }
-        __syncwarp();
-        if (lane < 16 && flags) {
-            const long long r = base + lane;
-            if (r < n) {
-                bool out = false;
-                for (int k = 0; k < NIN; ++k) {
-                    const float v = xs[lane * XP + k];
-                    out |= !(v >= hlo[k] && v <= hhi[k]);
-                }
-                // a cell without absorbed power emits nothing: no fallback needed
-                flags[r] = (out && total[r] > 0.0) ? 1 : 0;
+        const float* xs = xbuf + buf * 16 * NIN;  // [16][32]; rows past n hold stale values
+        // ---- hull check: row i, lane = feature; one ballot per row
+        if (flags) {
+            bool mine = false;
+            const float lo_f = hlo[lane], hi_f = hhi[lane];
+#pragma unroll 4
+            for (int i = 0; i < 16; ++i) {
+                const float v = xs[i * NIN + lane];
+                const unsigned out = __ballot_sync(0xffffffffu, !(v >= lo_f && v <= hi_f));
+                if (lane == i) mine = out != 0;
             }
+            const long long r = base + lane;
+            // a cell without absorbed power emits nothing: no fallback needed
+            if (lane < 16 && r < n) flags[r] = (mine && total[r] > 0.0) ? 1 : 0;
         }
         uint32_t a1[2][4];
 #pragma unroll
         for (int kk = 0; kk < 2; ++kk) {
             const int c = 16 * kk + 2 * t;
-            auto sx = [&](int row, int col) { return (xs[row * XP + col] - mean[col]) * istd[col]; };
+            auto sx = [&](int row, int col) { return (xs[row * NIN + col] - mean[col]) * istd[col]; };
             a1[kk][0] = pack_bf16(sx(g, c), sx(g, c + 1));
             a1[kk][1] = pack_bf16(sx(g + 8, c), sx(g + 8, c + 1));
             a1[kk][2] = pack_bf16(sx(g, c + 8), sx(g, c + 9));
@@ -250,6 +319,7 @@ __global__ void __launch_bounds__(32 * INF_WARPS, 2) mlp_infer_kernel(
                            make_double2(widen_pos(f1 * z[j][2]), widen_pos(f1 * z[j][3])));
             }
         }
+        __syncwarp();  // every lane is done with this buffer before it is refilled
     }
 }
 
@@ -549,10 +619,14 @@ static int repack(skirt_mlp_s* net, cudaStream_t s)
 int mlp_forward_internal(skirt_mlp_s* net, const float* features, const double* total, long long n, double* emission,
                          unsigned char* flags, cudaStream_t s)
 {
+    if ((reinterpret_cast<uintptr_t>(features) & 15) != 0)
+        return set_error(SKIRT_ERR_INVALID_ARG, "features must be 16-byte aligned");
     if (!net->packed) {
         int r = repack(net, s);
         if (r) return r;
     }
+    const unsigned zero = 0;
+    MCK(cudaMemcpyToSymbolAsync(g_mlp_timeout, &zero, sizeof zero, 0, cudaMemcpyHostToDevice, s));
     MCK(cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_TOTAL));
     int sms = 0, dev = 0, per_sm = 0;
     MCK(cudaGetDevice(&dev));
@@ -565,6 +639,14 @@ int mlp_forward_internal(skirt_mlp_s* net, const float* features, const double* 
     mlp_infer_kernel<<<(int)grid, 32 * INF_WARPS, SM_TOTAL, s>>>(net->Wb, net->Bb, net->stats, features, total, n,
                                                                   emission, flags);
     MCK(cudaGetLastError());
+    return SKIRT_OK;
+}
+
+int mlp_check_timeout()
+{
+    unsigned v = 0;
+    MCK(cudaMemcpyFromSymbol(&v, g_mlp_timeout, sizeof v));
+    if (v) return set_error(SKIRT_ERR_CUDA, "surrogate inference: a feature copy did not complete in time");
     return SKIRT_OK;
 }
 
@@ -908,5 +990,5 @@ extern "C" int skirt_mlp_forward(skirt_mlp_t net, const float* features, const d
     int r = mlp_forward_internal(net, features, total, n, emission, flags, s);
     if (r) return r;
     MCK(cudaStreamSynchronize(s));
-    return SKIRT_OK;
+    return mlp_check_timeout();
 }

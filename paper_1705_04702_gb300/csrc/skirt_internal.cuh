@@ -193,6 +193,9 @@ namespace skirt {
 // mlp.cu: tensor-core inference of the emission surrogate (stream-ordered, no sync)
 int mlp_forward_internal(skirt_mlp_s* net, const float* features, const double* total, long long n,
                          double* emission, unsigned char* flags, cudaStream_t s);
+// after the stream has synchronised: INVALID (CUDA) when an inference launch
+// gave up waiting for a feature copy
+int mlp_check_timeout();
 // emission.cu: exact FP64 emission of rows (all rows when rows == NULL); a
 // second absorbed table [ncell][n2] with its shares (NULL: none) adds its power
 int launch_exact_emission(const double* absorbed, int n_in, const double* w_dev, const float* mass,
