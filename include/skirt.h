@@ -131,9 +131,13 @@ enum { SKIRT_REC_FIELDS = 8 };
 
 typedef struct {
     int precision;     /* SKIRT_PREC_FP64: the plain form, FP64 throughout.
-                          SKIRT_PREC_MIXED: FP32 positions, directions, cell traversal and
-                          phase-function sampling; FP64 cumulative optical depth, packet
-                          luminosity, and all tallies. */
+                          SKIRT_PREC_MIXED: FP32 directions, cell traversal, phase-function
+                          sampling and packet luminosity; positions as FP32 (hi, lo) pairs;
+                          the cumulative optical depth of a traversal summed error-free
+                          (double-float) and formed in FP64 at every event; all tallies and
+                          the energy ledger in FP64.  A deposit or peel-off traversal ends
+                          once its optical depth exceeds 30 (what is left is below 1e-13 of
+                          the packet's luminosity). */
     int schedule;      /* SKIRT_SCHED_PER_LAMBDA: one launch per wavelength, one packet per
                           thread.  SKIRT_SCHED_PERSISTENT: one persistent launch for all
                           wavelengths; threads refill from a global work queue. */
@@ -183,6 +187,10 @@ typedef struct {
  * images and sed may be NULL when ninstr == 0.  ledger (host) may be NULL;
  * ledger_per_lambda (host double[n][4], emitted/absorbed/escaped/residual)
  * may be NULL.
+ * With n > 1 the packets deposit into a wavelength-major copy of the
+ * absorbed table ([n][ncell], grid scratch of the same size as the table)
+ * that one transpose turns into the [ncell][n] result (or adds to it with
+ * accumulate); without room for the copy they deposit in place.
  * Limits: npackets[j] < 2^32; 0 <= ninstr <= 16.
  * Errors: INVALID_ARG, OOM, CUDA; EVENT_CAP / NONFINITE / SOURCE after a
  * completed trace whose ledger flagged the condition. */
@@ -194,10 +202,12 @@ int skirt_trace(skirt_grid_t grid, const skirt_source* src, const skirt_waveleng
 /* Autotuner (the GPU counterpart of choosing the hybrid scheme for the
  * hardware, Sect. 6.2): times the persistent schedule on a sample of
  * the workload (every npackets[j] scaled by sample_fraction, at least one
- * packet where npackets[j] > 0) over block sizes {64,128,256,512}, refill
- * chunks {1,2,4,8,16} and 1..max resident blocks per SM, and writes the
- * fastest block / chunk / blocks_per_sm into *opts.  The outputs are used as
- * scratch and left zeroed.  Errors as skirt_trace. */
+ * packet where npackets[j] > 0) over block sizes {64, 128, 256} (and 512 for
+ * the FP64 form), refill chunks {1, 4, 16}, step_min {16, 20, 24} (mixed
+ * form) and resident blocks per SM from the occupancy limit down, halving,
+ * and writes the fastest block / chunk / blocks_per_sm / step_min into
+ * *opts.  The outputs are used as scratch and left zeroed.  Errors as
+ * skirt_trace. */
 int skirt_autotune(skirt_grid_t grid, const skirt_source* src, const skirt_wavelengths* wl,
                    const uint64_t* npackets, uint64_t seed, const skirt_instrument* ins, int ninstr,
                    skirt_trace_opts* opts, double sample_fraction, double* absorbed,
@@ -283,9 +293,11 @@ int skirt_mlp_grad(skirt_mlp_t net, const float* x_std, const float* target, int
                    void* stream);
 
 /* Tensor-core inference: emission (device double[n][100]) = softmax(MLP(
- * (features - mean) / std)) * total (device double[n]).  If flags is not
- * NULL (device unsigned char[n]) it receives 1 for rows with total > 0 whose
- * features fall outside the hull. */
+ * (features - mean) / std)) * total (device double[n]).  features: device
+ * float[n][32], 16-byte aligned (its 128-byte rows are fetched by bulk
+ * asynchronous copies).  If flags is not NULL (device unsigned char[n]) it
+ * receives 1 for rows with total > 0 whose features fall outside the hull.
+ * Errors: INVALID_ARG (also for unaligned features), CUDA. */
 int skirt_mlp_forward(skirt_mlp_t net, const float* features, const double* total, long long n,
                       double* emission, unsigned char* flags, void* stream);
 
