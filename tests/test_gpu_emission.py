@@ -166,3 +166,28 @@ def test_training_reaches_two_percent_and_fallback_is_exact(S):
     ref2, _, _ = E.exact_emission(a2, lam, m[n_train:n_train + 50].astype(np.float64))
     np.testing.assert_allclose(em2.cpu().numpy(), ref2, rtol=1e-9, atol=1e-12 * ref2.max())
     net.close()
+
+
+@pytest.mark.parametrize("n_in", [1, 700], ids=["one_wavelength", "700_wavelengths"])
+def test_band_features_and_exact_edges(S, n_in):
+    """One input wavelength (all power in the first band, the other 31 at the
+    floor) and 700 (22 staged column blocks per cell), on a cell count that
+    is not a multiple of 32."""
+    import torch
+    lam = np.geomspace(0.09, 10.0, n_in) if n_in > 1 else np.array([0.55])
+    n = 1001
+    a, m = W.absorbed_spectra(n, lam, seed=11)
+    a[5] = 0.0
+    feat = torch.zeros((n, 32), dtype=torch.float32, device="cuda")
+    tot = torch.zeros(n, dtype=torch.float64, device="cuda")
+    S.skirt_band_features(_dev(a, torch.float64), n, lam.size, lam, _dev(m, torch.float32), feat, tot)
+    B, x, total = E.band_features(a, lam, m.astype(np.float64))
+    np.testing.assert_allclose(tot.cpu().numpy(), total, rtol=1e-13, atol=0)
+    np.testing.assert_allclose(feat.cpu().numpy(), x, rtol=3e-7, atol=1e-6)
+    em = torch.zeros((n, 100), dtype=torch.float64, device="cuda")
+    S.skirt_dust_emission(_dev(a, torch.float64), n, lam.size, lam, _dev(m, torch.float32), S.EMIT_EXACT, None, em)
+    ref, _, _ = E.exact_emission(a, lam, m.astype(np.float64))
+    g = em.cpu().numpy()
+    big = ref > 1e-9 * ref.sum(axis=1, keepdims=True)
+    np.testing.assert_allclose(g[big], ref[big], rtol=1e-9)
+    assert np.all(g[5] == 0)
