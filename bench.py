@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--epochs", type=int, default=60, help="learned workload: training epochs")
+    ap.add_argument("--lr", type=float, default=2e-3, help="learned workload: Adam step size")
     ap.add_argument("--workload", default="disk", choices=["disk", "disk40", "torus", "learned", "selfabs"],
                     help="disk: 1 wavelength, --packets packets (default); disk40: 40 wavelengths, "
                          "--packets per wavelength; torus: clumpy torus, 200 wavelengths, uneven counts "
@@ -274,7 +276,7 @@ def run_learned_report(args):
     from paper_1705_04702_gb300.learned import run_learned
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     rep = run_learned(n=args.grid, nlambda=200, packet_scale=args.packets / 1e8, n_train=1_000_000,
-                      n_test=100_000, epochs=20, reemit_per_lambda=1_000_000)
+                      n_test=100_000, epochs=args.epochs, lr=args.lr, reemit_per_lambda=1_000_000)
     rep = {k: v for k, v in rep.items() if not k.startswith("_")}
     print(json.dumps({"report": "learned form", "workload": f"clumpy torus {args.grid}^3, 200 wavelengths",
                       **rep}), flush=True)
