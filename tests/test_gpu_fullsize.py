@@ -110,3 +110,62 @@ def test_torus_256_fp64_histories_follow_the_oracle(S, oracle_lib):
     rec = g["records"].cpu().numpy()
     compare_records(rec, r["records"], small, REL_FP64, 0.99, same_n_min=1.0)
     compare_records(rec, r["records"], small, 1e-7, 0.999, same_n_min=1.0)
+
+
+def test_learned_form_full_grid_sampled(S, oracle_lib):
+    """The learned form on the full 256^3 clumpy torus (16.8M cells, 200
+    wavelengths; the absorbed table from a 5% stellar trace): band features
+    and the exact emission on every cell, the oracle on 2000 sampled heated
+    cells; energy exact on every cell; the surrogate (trained on 500k cells,
+    60 epochs) energy-exact on every cell and within 2% of the exact rows
+    (median)."""
+    import torch
+    from oracle import emission as E
+    prob = W.torus_problem(n=256, nlambda=200, npx=64, packet_scale=0.05)
+    grid = S.Grid(prob.grid)
+    ncell, nl = grid.ncell, prob.wl.n
+    absorbed = torch.zeros((ncell, nl), dtype=torch.float64, device="cuda")
+    opts = S.skirt_trace_opts_default()
+    opts.peel = 0
+    tables = S.Tables(prob.wl)
+    S.skirt_trace(grid.h, S.make_source(prob.source), tables.c, prob.npk, prob.seed, [], opts, absorbed, None, None)
+    mass = torch.empty(ncell, dtype=torch.float32, device="cuda")
+    S.skirt_dust_mass(grid.h, mass)
+    feat = torch.empty((ncell, 32), dtype=torch.float32, device="cuda")
+    tot = torch.empty(ncell, dtype=torch.float64, device="cuda")
+    lam = np.ascontiguousarray(prob.wl.lam)
+    S.skirt_band_features(absorbed, ncell, nl, lam, mass, feat, tot)
+    exact = torch.empty((ncell, 100), dtype=torch.float64, device="cuda")
+    S.skirt_dust_emission(absorbed, ncell, nl, lam, mass, S.EMIT_EXACT, None, exact)
+    live = torch.nonzero((tot > 0) & (mass > 0)).flatten()
+    assert live.numel() > 1_000_000
+    # energy: every heated row sums to its absorbed power
+    rel = ((exact.index_select(0, live).sum(dim=1) - tot.index_select(0, live)).abs() / tot.index_select(0, live))
+    assert float(rel.max()) < 1e-12
+    # sampled cells against the oracle
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    pick = live[torch.randperm(live.numel(), device="cuda", generator=gen)[:2000]]
+    a_s = absorbed.index_select(0, pick).cpu().numpy()
+    m_s = mass.index_select(0, pick).cpu().numpy().astype(np.float64)
+    _, x_ref, t_ref = E.band_features(a_s, lam, m_s)
+    np.testing.assert_allclose(tot.index_select(0, pick).cpu().numpy(), t_ref, rtol=1e-13)
+    np.testing.assert_allclose(feat.index_select(0, pick).cpu().numpy(), x_ref, rtol=3e-7, atol=1e-6)
+    e_ref, _, _ = E.exact_emission(a_s, lam, m_s)
+    g = exact.index_select(0, pick).cpu().numpy()
+    big = e_ref > 1e-9 * e_ref.sum(axis=1, keepdims=True)
+    np.testing.assert_allclose(g[big], e_ref[big], rtol=1e-9)
+    # the surrogate on every cell
+    tr = live[torch.randperm(live.numel(), device="cuda", generator=gen)[:500_000]]
+    net = S.MLP(seed=6)
+    net.train(feat.index_select(0, tr).contiguous(), exact.index_select(0, tr).contiguous(), tr.numel(), epochs=60)
+    sur = torch.empty_like(exact)
+    st = S.skirt_dust_emission(absorbed, ncell, nl, lam, mass, S.EMIT_SURROGATE, net, sur)
+    net.close()
+    grid.close()
+    assert st["n_cells"] == ncell
+    rs = (sur.index_select(0, live).sum(dim=1) - tot.index_select(0, live)).abs() / tot.index_select(0, live)
+    assert float(rs.max()) < 1e-5
+    e = (torch.linalg.vector_norm(sur.index_select(0, pick) - exact.index_select(0, pick), dim=1) /
+         torch.linalg.vector_norm(exact.index_select(0, pick), dim=1)).cpu().numpy()
+    assert np.median(e) < 0.02, np.median(e)
