@@ -105,13 +105,115 @@ static int og_index(double x, double lo, double d, int n)
     return (int)f;
 }
 
+/* ------------------------------------------------------------------------
+ * Octree grid (the adaptive grid of the paper's ERIS run, Sect. 7.9): the
+ * root box is split into 8 equal boxes, recursively, and the leaves hold the
+ * dust.  A leaf of level l at integer position (ix, iy, iz) spans
+ * [ix, ix+1) 2^(L-l) cells of the finest lattice (L levels) along x, and so
+ * on.  The oracle keeps its own pointer tree: node n has 8 consecutive
+ * children from child[n] on (-1: none) or is leaf leaf[n] (-1: not a leaf);
+ * child octant = x bit + 2 y bit + 4 z bit.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t* child;
+    int64_t* leaf;
+    int64_t n, cap;
+    int levels;
+} og_tree;
+
+static void og_tree_free(og_tree* T)
+{
+    free(T->child);
+    free(T->leaf);
+    T->child = NULL;
+    T->leaf = NULL;
+    T->n = T->cap = 0;
+}
+
+static int64_t og_tree_alloc8(og_tree* T)
+{
+    if (T->n + 8 > T->cap) {
+        int64_t cap = T->cap ? 2 * T->cap : 64;
+        while (cap < T->n + 8) cap *= 2;
+        T->child = (int32_t*)realloc(T->child, sizeof(int32_t) * (size_t)cap);
+        T->leaf = (int64_t*)realloc(T->leaf, sizeof(int64_t) * (size_t)cap);
+        T->cap = cap;
+    }
+    int64_t first = T->n;
+    for (int q = 0; q < 8; ++q) {
+        T->child[first + q] = -1;
+        T->leaf[first + q] = -1;
+    }
+    T->n += 8;
+    return first;
+}
+
+/* Inserts every leaf from the root down; returns 0, or -1 when a leaf lies
+ * outside the lattice, two leaves overlap, or the leaves leave a hole. */
+static int og_tree_build(const og_problem* P, og_tree* T)
+{
+    memset(T, 0, sizeof *T);
+    T->levels = P->oct_levels;
+    if (P->oct_levels < 1 || P->oct_levels > 20 || P->oct_nleaf < 1) return -1;
+    og_tree_alloc8(T); /* node 0 is the root; nodes 1..7 of this block stay unused */
+    for (int q = 1; q < 8; ++q) T->leaf[q] = -2;
+    for (int64_t m = 0; m < P->oct_nleaf; ++m) {
+        const int32_t* lf = P->oct_leaves + 4 * m;
+        int l = lf[0];
+        if (l < 0 || l > P->oct_levels) return -1;
+        for (int a = 1; a < 4; ++a)
+            if (lf[a] < 0 || (int64_t)lf[a] >= ((int64_t)1 << l)) return -1;
+        int64_t node = 0;
+        for (int d = 0; d < l; ++d) {
+            if (T->leaf[node] >= 0) return -1;
+            if (T->child[node] < 0) {
+                int64_t first = og_tree_alloc8(T);
+                if (first > 0x7fffffff) return -1;
+                T->child[node] = (int32_t)first;
+            }
+            int bit = l - 1 - d;
+            int oct = ((lf[1] >> bit) & 1) | (((lf[2] >> bit) & 1) << 1) | (((lf[3] >> bit) & 1) << 2);
+            node = T->child[node] + oct;
+        }
+        if (T->leaf[node] >= 0 || T->child[node] >= 0) return -1;
+        T->leaf[node] = m;
+    }
+    for (int64_t node = 0; node < T->n; ++node)
+        if (T->leaf[node] == -1 && T->child[node] < 0) return -1;
+    return 0;
+}
+
+/* The leaf holding finest-lattice cell (j0, j1, j2). */
+static int64_t og_tree_find(const og_tree* T, int j0, int j1, int j2)
+{
+    int64_t node = 0;
+    for (int d = 0; T->leaf[node] < 0; ++d) {
+        int bit = T->levels - 1 - d;
+        int oct = ((j0 >> bit) & 1) | (((j1 >> bit) & 1) << 1) | (((j2 >> bit) & 1) << 2);
+        node = T->child[node] + oct;
+    }
+    return T->leaf[node];
+}
+
+int og_octree_check(const og_problem* P)
+{
+    og_tree T;
+    int r = og_tree_build(P, &T);
+    og_tree_free(&T);
+    return r;
+}
+
 /* Cells crossed by the ray p + t k (t > 0) up to the grid boundary, with the
  * length inside each.  Every interior face plane the ray crosses before the
  * exit is listed per axis (each list is already sorted in t), the lists are
  * merged, and each non-empty interval between consecutive crossings is
- * attributed to the cell containing its midpoint.  Returns the number of
- * segments, or -1 if `cap` is too small. */
-int og_path(const og_problem* P, const double p[3], const double k[3], int* cells, double* lens, int cap)
+ * attributed to the cell containing its midpoint.  On an octree the planes
+ * are those of the finest lattice, every interval lies in one lattice cell
+ * and so in one leaf, and consecutive intervals in the same leaf (a box,
+ * entered once) form one segment from its first to its last crossing.
+ * Returns the number of segments, or -1 if `cap` is too small. */
+static int og_path_tree(const og_problem* P, const og_tree* T, const double p[3], const double k[3], int* cells,
+                        double* lens, int cap)
 {
     double lo[3], hi[3], d[3];
     int n[3];
@@ -138,7 +240,7 @@ int og_path(const og_problem* P, const double p[3], const double k[3], int* cell
     }
 
     int head[3] = {0, 0, 0};
-    double tprev = 0.0;
+    double tprev = 0.0, tseg = 0.0;
     int nseg = 0;
     for (;;) {
         double tnext = texit;
@@ -147,20 +249,36 @@ int og_path(const og_problem* P, const double p[3], const double k[3], int* cell
         for (int a = 0; a < 3; ++a)
             while (head[a] < cnt[a] && ts[a][head[a]] <= tnext) head[a]++;
         if (tnext > tprev) {
-            if (nseg >= cap) { nseg = -1; break; }
             double tm = 0.5 * (tprev + tnext);
             int ix = og_index(p[0] + tm * k[0], lo[0], d[0], n[0]);
             int iy = og_index(p[1] + tm * k[1], lo[1], d[1], n[1]);
             int iz = og_index(p[2] + tm * k[2], lo[2], d[2], n[2]);
-            cells[nseg] = (iz * n[1] + iy) * n[0] + ix;
-            lens[nseg] = tnext - tprev;
-            nseg++;
+            int cell = T ? (int)og_tree_find(T, ix, iy, iz) : (iz * n[1] + iy) * n[0] + ix;
+            if (T && nseg > 0 && cells[nseg - 1] == cell) {
+                lens[nseg - 1] = tnext - tseg;
+            } else {
+                if (nseg >= cap) { nseg = -1; break; }
+                cells[nseg] = cell;
+                lens[nseg] = tnext - tprev;
+                tseg = tprev;
+                nseg++;
+            }
         }
         tprev = tnext;
         if (tnext >= texit) break;
     }
     for (int a = 0; a < 3; ++a) free(ts[a]);
     return nseg;
+}
+
+int og_path(const og_problem* P, const double p[3], const double k[3], int* cells, double* lens, int cap)
+{
+    if (P->oct_levels <= 0) return og_path_tree(P, NULL, p, k, cells, lens, cap);
+    og_tree T;
+    int r = -1;
+    if (og_tree_build(P, &T) == 0) r = og_path_tree(P, &T, p, k, cells, lens, cap);
+    og_tree_free(&T);
+    return r;
 }
 
 /* ------------------------------------------------------------------------

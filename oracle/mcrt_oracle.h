@@ -15,7 +15,7 @@ extern "C" {
 #endif
 
 enum { OG_SRC_POINT = 0, OG_SRC_DISK = 1, OG_SRC_BEAM = 2, OG_SRC_DUST = 3 };
-enum { OG_ERR_EVENT_CAP = 1, OG_ERR_SOURCE = 2, OG_ERR_NONFINITE = 4 };
+enum { OG_ERR_EVENT_CAP = 1, OG_ERR_SOURCE = 2, OG_ERR_NONFINITE = 4, OG_ERR_TREE = 8 };
 enum { OG_REC_FIELDS = 8 };
 
 typedef struct {
@@ -56,6 +56,13 @@ typedef struct {
     int nrec;         /* per-packet records for packet indices < nrec */
     double* records;  /* [nlambda][nrec][8] */
     int status;       /* OR of OG_ERR_* */
+    /* octree grid instead of the regular one when oct_levels > 0: the root
+       box is bbox, nx = ny = nz = 2^oct_levels is the finest lattice, and
+       oct_leaves[m] = (level, ix, iy, iz) places leaf m at its own level;
+       kr, absorbed and cell_cdf are then indexed by leaf */
+    int oct_levels;
+    int64_t oct_nleaf;
+    const int32_t* oct_leaves;
 } og_problem;
 
 void og_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -64,6 +71,7 @@ int og_path(const og_problem* P, const double p[3], const double k[3], int* cell
 double og_hg_mu(double g, double u);
 void og_rotate(const double k[3], double mu, double phi, double out[3]);
 int og_trace(og_problem* P);
+int og_octree_check(const og_problem* P);
 
 #ifdef __cplusplus
 }
