@@ -29,7 +29,7 @@ _lock = threading.Lock()
 _lib = None
 
 REC_FIELDS = 8
-ERR_EVENT_CAP, ERR_SOURCE, ERR_NONFINITE = 1, 2, 4
+ERR_EVENT_CAP, ERR_SOURCE, ERR_NONFINITE, ERR_TREE = 1, 2, 4, 8
 
 
 def build(force: bool = False) -> str:
@@ -79,6 +79,9 @@ class _Problem(ctypes.Structure):
         ("nrec", ctypes.c_int),
         ("records", ctypes.POINTER(ctypes.c_double)),
         ("status", ctypes.c_int),
+        ("oct_levels", ctypes.c_int),
+        ("oct_nleaf", ctypes.c_int64),
+        ("oct_leaves", ctypes.POINTER(ctypes.c_int32)),
     ]
 
 
@@ -103,6 +106,8 @@ def lib():
             L.og_rotate.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_double, ctypes.c_double,
                                     ctypes.POINTER(ctypes.c_double)]
             L.og_rotate.restype = None
+            L.og_octree_check.argtypes = [ctypes.POINTER(_Problem)]
+            L.og_octree_check.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -189,6 +194,12 @@ def _make_problem(prob, keep, pk_begin=0, pk_end=None, nrec=0, peel=True, cell_c
         P.ledger, P.counters, P.records = _dp(keep.ledger), _dp(keep.counters), _dp(keep.records)
         P.nrec = int(nrec)
     P.status = 0
+    leaves = getattr(g, "leaves", None)
+    if leaves is not None:
+        keep.leaves = np.ascontiguousarray(leaves, dtype=np.int32).reshape(-1)
+        P.oct_levels = int(g.max_level)
+        P.oct_nleaf = int(g.ncell)
+        P.oct_leaves = keep.leaves.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
     return P
 
 
@@ -221,6 +232,19 @@ def trace(prob, pk_begin=0, pk_end=None, nrec=0, peel=True, cell_cdf=None):
         "records": keep.records[:, :nrec] if nrec else keep.records[:, :0],
         "status": int(status),
     }
+
+
+def octree_valid(grid) -> bool:
+    """True when the leaves of an octree description tile its root box."""
+    keep = _Keep()
+    P = _Problem()
+    P.nx = P.ny = P.nz = grid.nx
+    P.bbox = (ctypes.c_double * 6)(*[float(v) for v in grid.bbox])
+    keep.leaves = np.ascontiguousarray(grid.leaves, dtype=np.int32).reshape(-1)
+    P.oct_levels = int(grid.max_level)
+    P.oct_nleaf = int(grid.ncell)
+    P.oct_leaves = keep.leaves.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    return lib().og_octree_check(ctypes.byref(P)) == 0
 
 
 def path(prob, p, k):

@@ -27,6 +27,10 @@
  *    (seed, packet, wavelength, event); termination at w_min of the launch
  *    luminosity, the last scattering still peeled off, the remainder booked
  *    as "residual"; distant-observer instruments.
+ *  - Sect. 7.9 runs on an octree dust grid (up to 13 division levels); its
+ *    cells are the leaves of a recursive split of the root box into 8 equal
+ *    boxes.  The grid is either regular or such a tree; the tree's paths
+ *    come from the planes of its finest lattice (see og_path_tree).
  */
 #include "mcrt_oracle.h"
 
@@ -336,6 +340,7 @@ typedef struct {
     int* cells;
     double* lens;
     int cap;
+    const og_tree* tree; /* octree grid, else NULL */
     /* per-packet record */
     double escaped, absorbed, residual, peel;
 } og_work;
@@ -368,7 +373,7 @@ static void og_peel(og_problem* P, int lam, const double x[3], const double* wei
                         kobs[2] * e1[0] - kobs[0] * e1[2],
                         kobs[0] * e1[1] - kobs[1] * e1[0]};
         if (weight[q] > 0.0) {
-            int nseg = og_path(P, x, kobs, W->cells, W->lens, W->cap);
+            int nseg = og_path_tree(P, W->tree, x, kobs, W->cells, W->lens, W->cap);
             if (nseg < 0) { P->status |= OG_ERR_NONFINITE; nseg = 0; }
             P->counters[3] += (double)nseg;
             double tau = og_tau(P, lam, W->cells, W->lens, nseg);
@@ -438,7 +443,7 @@ static int og_launch(og_problem* P, int lam, uint64_t i, double x[3], double k[3
         double lo[3], hi[3], d[3];
         int n[3];
         og_axes(P, lo, hi, d, n);
-        size_t ncell = (size_t)n[0] * n[1] * n[2];
+        size_t ncell = P->oct_levels > 0 ? (size_t)P->oct_nleaf : (size_t)n[0] * n[1] * n[2];
         const double* cdf = P->cell_cdf + (size_t)lam * ncell;
         og_draw(P, lam, i, 0u, 0u, u);
         size_t a0 = 0, a1 = ncell - 1; /* first cell with cdf > u */
@@ -447,6 +452,15 @@ static int og_launch(og_problem* P, int lam, uint64_t i, double x[3], double k[3
             if (cdf[mid] > u[0]) a1 = mid; else a0 = mid + 1;
         }
         size_t m = a0;
+        if (P->oct_levels > 0) {
+            /* leaf box: lattice corner c = index << (L - level), side 2^(L - level) */
+            const int32_t* lf = P->oct_leaves + 4 * m;
+            int shift = P->oct_levels - lf[0];
+            double side = (double)(1 << shift);
+            for (int a = 0; a < 3; ++a)
+                x[a] = lo[a] + ((double)(lf[1 + a] << shift) + u[1 + a] * side) * d[a];
+            break;
+        }
         int ix = (int)(m % (size_t)n[0]);
         int iy = (int)((m / (size_t)n[0]) % (size_t)n[1]);
         int iz = (int)(m / ((size_t)n[0] * n[1]));
@@ -489,7 +503,7 @@ static void og_packet(og_problem* P, int lam, uint64_t i, og_work* W)
          * grid boundary: segment m with optical depth dtau_m, cumulative
          * tau_{m-1} before it, receives L (1-albedo)(e^{-tau_{m-1}} -
          * e^{-tau_m}) = L (1-albedo) e^{-tau_{m-1}} (1 - e^{-dtau_m}). */
-        int nseg = og_path(P, x, k, W->cells, W->lens, W->cap);
+        int nseg = og_path_tree(P, W->tree, x, k, W->cells, W->lens, W->cap);
         if (nseg < 0) { P->status |= OG_ERR_NONFINITE; nseg = 0; }
         P->counters[1] += (double)nseg;
         double tau = 0.0;
@@ -595,6 +609,16 @@ int og_trace(og_problem* P)
 {
     if (P->ninstr > 64) return -1;
     og_work W;
+    og_tree T;
+    W.tree = NULL;
+    if (P->oct_levels > 0) {
+        if (og_tree_build(P, &T) != 0) {
+            og_tree_free(&T);
+            P->status |= OG_ERR_TREE;
+            return P->status;
+        }
+        W.tree = &T;
+    }
     W.cap = P->nx + P->ny + P->nz + 8;
     W.cells = (int*)malloc(sizeof(int) * (size_t)W.cap);
     W.lens = (double*)malloc(sizeof(double) * (size_t)W.cap);
@@ -604,5 +628,6 @@ int og_trace(og_problem* P)
     }
     free(W.cells);
     free(W.lens);
+    if (W.tree) og_tree_free(&T);
     return P->status;
 }
