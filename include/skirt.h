@@ -74,6 +74,26 @@ const char* skirt_version(void);
 typedef struct skirt_grid_s* skirt_grid_t;
 int skirt_grid_create(skirt_grid_t* out, int nx, int ny, int nz, const double bbox[6],
                       const float* kr);
+/* Octree dust grid (the adaptive grid of the ERIS run, Sect. 7.9: up to 13
+ * division levels, 8.2 million cells).  The root box bbox is split into 8
+ * equal boxes, recursively; the leaves are the cells.  Leaf m (0 <= m <
+ * nleaf) is leaves[4m .. 4m+3] = {level, ix, iy, iz}: the box at integer
+ * position (ix, iy, iz) among the 2^level boxes per axis of that level
+ * (0 <= level <= max_level, 0 <= ix, iy, iz < 2^level).  The leaves must
+ * tile the root box exactly: no overlap, no hole.  Every per-cell table of
+ * the library (absorbed, dust-source emission, mass, features) is then
+ * indexed by leaf in this order.
+ *
+ * max_level: 1 .. 15.  leaves: host int32[nleaf][4], read during the call.
+ * kr: device-or-host float[nleaf] as for skirt_grid_create.  nleaf < 2^27.
+ * The library builds a node array with the face neighbours of every leaf
+ * (the neighbour of the same or a larger size) on the device and copies kr.
+ * Traversal: the FP64 form (precision SKIRT_PREC_FP64) and the mixed form.
+ * Errors: INVALID_ARG for sizes, values or leaves that do not tile the box
+ * (the message names the first offending leaf), OOM, CUDA. */
+int skirt_octree_create(skirt_grid_t* out, int max_level, const double bbox[6], long long nleaf,
+                        const int32_t* leaves, const float* kr);
+
 /* Frees the grid and all scratch attached to it.  NULL is accepted. */
 int skirt_grid_destroy(skirt_grid_t grid);
 
@@ -238,7 +258,8 @@ enum { SKIRT_MLP_NPARAM = 128 * 32 + 128 + 128 * 128 + 128 + 100 * 128 + 100 };
  * weights W[100] (host arrays, either may be NULL). */
 int skirt_emission_grid(double* lambda_um, double* weights);
 
-/* Dust mass of every cell, M = kr * cell volume (device float[ncell]). */
+/* Dust mass of every cell, M = kr * cell volume (the leaf's box on an
+ * octree grid), device float[ncell]. */
 int skirt_dust_mass(skirt_grid_t grid, float* mass, void* stream);
 
 /* Band compression: B_b(m) = sum of absorbed(m, j) over the input

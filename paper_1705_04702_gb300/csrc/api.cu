@@ -151,34 +151,17 @@ extern "C" int skirt_trace_opts_default(skirt_trace_opts* o)
 }
 
 // ------------------------------------------------------------------------ grid
-extern "C" int skirt_grid_create(skirt_grid_t* out, int nx, int ny, int nz, const double bbox[6], const float* kr)
+namespace skirt {
+
+int grid_init(skirt_grid_s* g, int nx, int ny, int nz, long long ncell, const double bbox[6], const float* kr)
 {
-    if (!out) return fail(SKIRT_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
-    if (nx < 1 || ny < 1 || nz < 1) return fail(SKIRT_ERR_INVALID_ARG, "grid sizes must be >= 1");
-    const long long ncell = (long long)nx * ny * nz;
-    if (ncell >= (1ll << 31)) return fail(SKIRT_ERR_INVALID_ARG, "ncell must be < 2^31");
-    if (!bbox || !kr) return fail(SKIRT_ERR_INVALID_ARG, "bbox / kr is NULL");
-    if (!finite_all(bbox, 6)) return fail(SKIRT_ERR_INVALID_ARG, "bbox must be finite");
-    for (int a = 0; a < 3; ++a)
-        if (!(bbox[2 * a] < bbox[2 * a + 1])) return fail(SKIRT_ERR_INVALID_ARG, "bbox axis %d is empty", a);
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
-        cudaGetLastError();
-        return fail(SKIRT_ERR_NO_DEVICE, "no CUDA device");
-    }
-    skirt_grid_s* g = new skirt_grid_s;
-    auto bail = [&](int code) {
-        skirt_grid_destroy(g);
-        return code;
-    };
     cudaError_t e;
-    if ((e = cudaGetDevice(&g->device)) != cudaSuccess) return bail(fail(SKIRT_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e)));
+    if ((e = cudaGetDevice(&g->device)) != cudaSuccess) return fail(SKIRT_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device);
     g->nx = nx; g->ny = ny; g->nz = nz; g->ncell = ncell;
     std::memcpy(g->bbox, bbox, sizeof g->bbox);
-    if ((e = cudaMalloc(&g->kr32, sizeof(float) * ncell)) != cudaSuccess) return bail(fail(SKIRT_ERR_OOM, "kr32: %s", cudaGetErrorString(e)));
-    if ((e = cudaMalloc(&g->kr64, sizeof(double) * ncell)) != cudaSuccess) return bail(fail(SKIRT_ERR_OOM, "kr64: %s", cudaGetErrorString(e)));
+    if ((e = cudaMalloc(&g->kr32, sizeof(float) * ncell)) != cudaSuccess) return fail(SKIRT_ERR_OOM, "kr32: %s", cudaGetErrorString(e));
+    if ((e = cudaMalloc(&g->kr64, sizeof(double) * ncell)) != cudaSuccess) return fail(SKIRT_ERR_OOM, "kr64: %s", cudaGetErrorString(e));
     {
         // face planes lo + k d (k < n) and the upper bound, split into (hi, lo) FP32 pairs
         std::vector<float2> f;
@@ -192,24 +175,62 @@ extern "C" int skirt_grid_create(skirt_grid_t* out, int nx, int ny, int nz, cons
             }
         }
         if ((e = cudaMalloc(&g->faces, sizeof(float2) * f.size())) != cudaSuccess)
-            return bail(fail(SKIRT_ERR_OOM, "faces: %s", cudaGetErrorString(e)));
+            return fail(SKIRT_ERR_OOM, "faces: %s", cudaGetErrorString(e));
         if ((e = cudaMemcpy(g->faces, f.data(), sizeof(float2) * f.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
-            return bail(fail(SKIRT_ERR_CUDA, "faces: %s", cudaGetErrorString(e)));
+            return fail(SKIRT_ERR_CUDA, "faces: %s", cudaGetErrorString(e));
     }
     if ((e = cudaEventCreate(&g->ev0)) != cudaSuccess || (e = cudaEventCreate(&g->ev1)) != cudaSuccess)
-        return bail(fail(SKIRT_ERR_CUDA, "event: %s", cudaGetErrorString(e)));
+        return fail(SKIRT_ERR_CUDA, "event: %s", cudaGetErrorString(e));
     if ((e = cudaStreamCreateWithFlags(&g->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
-        return bail(fail(SKIRT_ERR_CUDA, "stream: %s", cudaGetErrorString(e)));
+        return fail(SKIRT_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
     if ((e = cudaMemcpy(g->kr32, kr, sizeof(float) * ncell, cudaMemcpyDefault)) != cudaSuccess)
-        return bail(fail(SKIRT_ERR_CUDA, "copy kr: %s", cudaGetErrorString(e)));
-    if ((e = g->scratch.ensure(256)) != cudaSuccess) return bail(fail(SKIRT_ERR_OOM, "scratch: %s", cudaGetErrorString(e)));
+        return fail(SKIRT_ERR_CUDA, "copy kr: %s", cudaGetErrorString(e));
+    if ((e = g->scratch.ensure(256)) != cudaSuccess) return fail(SKIRT_ERR_OOM, "scratch: %s", cudaGetErrorString(e));
     unsigned int* bad_d = (unsigned int*)g->scratch.p;
     unsigned int bad = 0;
     if ((e = cudaMemset(bad_d, 0, sizeof(unsigned int))) != cudaSuccess ||
         (e = launch_f32_to_f64(g->kr32, g->kr64, ncell, bad_d, 0)) != cudaSuccess ||
         (e = cudaMemcpy(&bad, bad_d, sizeof bad, cudaMemcpyDeviceToHost)) != cudaSuccess)
-        return bail(fail(SKIRT_ERR_CUDA, "convert kr: %s", cudaGetErrorString(e)));
-    if (bad) return bail(fail(SKIRT_ERR_INVALID_ARG, "kr holds negative or non-finite values"));
+        return fail(SKIRT_ERR_CUDA, "convert kr: %s", cudaGetErrorString(e));
+    if (bad) return fail(SKIRT_ERR_INVALID_ARG, "kr holds negative or non-finite values");
+    return SKIRT_OK;
+}
+
+int check_bbox(const double* bbox)
+{
+    if (!finite_all(bbox, 6)) return fail(SKIRT_ERR_INVALID_ARG, "bbox must be finite");
+    for (int a = 0; a < 3; ++a)
+        if (!(bbox[2 * a] < bbox[2 * a + 1])) return fail(SKIRT_ERR_INVALID_ARG, "bbox axis %d is empty", a);
+    return SKIRT_OK;
+}
+
+int check_device()
+{
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(SKIRT_ERR_NO_DEVICE, "no CUDA device");
+    }
+    return SKIRT_OK;
+}
+
+}  // namespace skirt
+
+extern "C" int skirt_grid_create(skirt_grid_t* out, int nx, int ny, int nz, const double bbox[6], const float* kr)
+{
+    if (!out) return fail(SKIRT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(SKIRT_ERR_INVALID_ARG, "grid sizes must be >= 1");
+    const long long ncell = (long long)nx * ny * nz;
+    if (ncell >= (1ll << 31)) return fail(SKIRT_ERR_INVALID_ARG, "ncell must be < 2^31");
+    if (!bbox || !kr) return fail(SKIRT_ERR_INVALID_ARG, "bbox / kr is NULL");
+    if (int r = check_bbox(bbox)) return r;
+    if (int r = check_device()) return r;
+    skirt_grid_s* g = new skirt_grid_s;
+    if (int r = grid_init(g, nx, ny, nz, ncell, bbox, kr)) {
+        skirt_grid_destroy(g);
+        return r;
+    }
     *out = g;
     return SKIRT_OK;
 }
@@ -234,6 +255,8 @@ extern "C" int skirt_grid_destroy(skirt_grid_t g)
     if (g->kr32) cudaFree(g->kr32);
     if (g->kr64) cudaFree(g->kr64);
     if (g->faces) cudaFree(g->faces);
+    if (g->oct_nodes) cudaFree(g->oct_nodes);
+    if (g->oct_leaf) cudaFree(g->oct_leaf);
     g->scratch.release();
     g->stage.release();
     g->cdf.release();
@@ -323,6 +346,8 @@ int validate(skirt_grid_t g, const skirt_source* src, const skirt_wavelengths* w
     if (src->kind == SKIRT_SRC_DUST && !src->emission) return fail(SKIRT_ERR_INVALID_ARG, "dust source needs emission");
     if (opts->precision != SKIRT_PREC_FP64 && opts->precision != SKIRT_PREC_MIXED)
         return fail(SKIRT_ERR_INVALID_ARG, "unknown precision %d", opts->precision);
+    if (g->oct_levels > 0 && opts->precision != SKIRT_PREC_FP64)
+        return fail(SKIRT_ERR_INVALID_ARG, "octree grids are traced in the FP64 form");
     if (opts->schedule != SKIRT_SCHED_PER_LAMBDA && opts->schedule != SKIRT_SCHED_PERSISTENT)
         return fail(SKIRT_ERR_INVALID_ARG, "unknown schedule %d", opts->schedule);
     if (opts->block != 0 && (opts->block < 32 || opts->block % 32 ||
@@ -437,6 +462,11 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
     A.kr32 = g->kr32;
     A.kr64 = g->kr64;
     A.nx = g->nx; A.ny = g->ny; A.nz = g->nz;
+    A.ncell = g->ncell;
+    A.oct_levels = g->oct_levels;
+    A.oct_nodes = g->oct_nodes;
+    A.oct_leaf = g->oct_leaf;
+    A.oct_step_cap = g->nx + g->ny + g->nz + 8;
     const int nn[3] = {g->nx, g->ny, g->nz};
     for (int a = 0; a < 3; ++a) {
         A.lo[a] = g->bbox[2 * a];
@@ -510,7 +540,7 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
     const int block = opts->block > 0 ? opts->block : 256;
     int bps = opts->blocks_per_sm;
     if (bps <= 0) {
-        CK(trace_occupancy(opts->precision, block, &bps));
+        CK(trace_occupancy(opts->precision, block, &bps, g->oct_levels > 0));
         if (bps < 1) bps = 1;
     }
     const int pgrid = g->sm_count * bps;
@@ -668,7 +698,7 @@ extern "C" int skirt_autotune(skirt_grid_t g, const skirt_source* src, const ski
     for (int bi = 0; bi < 4; ++bi) {
         if (bi > 0 && blocks[bi] == blocks[bi - 1]) continue;
         int maxbps = 0;
-        CK(trace_occupancy(o.precision, blocks[bi], &maxbps));
+        CK(trace_occupancy(o.precision, blocks[bi], &maxbps, g->oct_levels > 0));
         if (maxbps < 1) continue;
         for (int ci = 0; ci < 3; ++ci) {
             for (int si = 0; si < (mixed ? 3 : 1); ++si) {

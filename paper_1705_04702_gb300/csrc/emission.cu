@@ -108,10 +108,13 @@ cudaError_t upload_model(cudaStream_t s)
     return cudaMemcpyToSymbolAsync(c_beta, BETA, sizeof BETA, 0, cudaMemcpyHostToDevice, s);
 }
 
-__global__ void dust_mass_kernel(const float* __restrict__ kr, long long n, float vol, float* __restrict__ mass)
+// vol: the cell volume; on an octree (leaf != NULL) the finest-lattice cell
+// volume, times 8^(levels - level) for each leaf
+__global__ void dust_mass_kernel(const float* __restrict__ kr, long long n, float vol, float* __restrict__ mass,
+                                 const int4* __restrict__ leaf, int levels)
 {
     for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (long long)gridDim.x * blockDim.x)
-        mass[m] = kr[m] * vol;
+        mass[m] = kr[m] * (leaf ? ldexpf(vol, 3 * (levels - leaf[m].w)) : vol);
 }
 
 // FP64 -> FP32 by truncation of the significand, on the integer pipe (GB300
@@ -582,7 +585,8 @@ extern "C" int skirt_dust_mass(skirt_grid_t g, float* mass, void* stream)
     if (!is_device(mass)) return set_error(SKIRT_ERR_INVALID_ARG, "mass must be device memory");
     const double vol = (g->bbox[1] - g->bbox[0]) / g->nx * (g->bbox[3] - g->bbox[2]) / g->ny *
                        (g->bbox[5] - g->bbox[4]) / g->nz;
-    dust_mass_kernel<<<grid_blocks(g->ncell, 256), 256, 0, (cudaStream_t)stream>>>(g->kr32, g->ncell, (float)vol, mass);
+    dust_mass_kernel<<<grid_blocks(g->ncell, 256), 256, 0, (cudaStream_t)stream>>>(g->kr32, g->ncell, (float)vol, mass,
+                                                                                  g->oct_leaf, g->oct_levels);
     ECK(cudaGetLastError());
     ECK(cudaStreamSynchronize((cudaStream_t)stream));
     return SKIRT_OK;

@@ -44,12 +44,28 @@ struct InstrDev {
     long long img_off;  // element offset of this instrument in the images array
 };
 
-enum { ERRBIT_EVENT_CAP = 1, ERRBIT_SOURCE = 2, ERRBIT_NONFINITE = 4 };
+enum { ERRBIT_EVENT_CAP = 1, ERRBIT_SOURCE = 2, ERRBIT_NONFINITE = 4, ERRBIT_PATH = 8 };
+
+// Octree node (32 bytes, one sector).  ref >= 0: internal node whose 8
+// children are nodes ref .. ref+7 (octant x + 2y + 4z); ref < 0: a leaf,
+// ~ref = level << 27 | leaf index (levels up to 15).  kr: the leaf's extinction coefficient.
+// nb[2a + (positive side)]: for a leaf, the node across that face along
+// axis a of the same level, or the leaf of a larger size that covers it
+// (-1 outside the root box).
+struct __align__(16) OctNode {
+    int ref;
+    float kr;
+    int nb[6];
+};
+constexpr int OCT_LEAF_BITS = 27;
+__host__ __device__ __forceinline__ int oct_leaf_index(int ref) { return (~ref) & ((1 << OCT_LEAF_BITS) - 1); }
+__host__ __device__ __forceinline__ int oct_leaf_level(int ref) { return (~ref) >> OCT_LEAF_BITS; }
 
 struct TraceArgs {
     const float* kr32;
     const double* kr64;
     int nx, ny, nz;
+    long long ncell;                       // nx*ny*nz, or the number of octree leaves
     double lo[3], d[3], hi[3];
     int nlambda;
     const double* kscale;
@@ -91,15 +107,21 @@ struct TraceArgs {
     unsigned long long q_base, q_count;    // per-wavelength schedule: this launch's packets
     int step_min;                          // mixed form: lanes still stepping below which a warp
                                            // switches to handling the events of its idle lanes
+    // octree grid (oct_levels > 0): nx = ny = nz = 2^oct_levels is the finest
+    // lattice, d its cell size; cells are leaves
+    int oct_levels;
+    const OctNode* oct_nodes;
+    const int4* oct_leaf;                  // per leaf: lattice corner x, y, z and level
+    int oct_step_cap;                      // crossings after which a traversal is abandoned
 };
 
 // trace.cu (FP64 form; dispatches the mixed form to trace_mixed.cu)
 cudaError_t launch_trace(const TraceArgs& a, int precision, int block, int grid, cudaStream_t s);
-cudaError_t trace_occupancy(int precision, int block, int* blocks_per_sm);
+cudaError_t trace_occupancy(int precision, int block, int* blocks_per_sm, bool octree);
 size_t trace_smem_bytes(int ninstr, int block);
 // trace_mixed.cu
 cudaError_t launch_trace_mixed(const TraceArgs& a, int block, int grid, cudaStream_t s);
-cudaError_t trace_mixed_occupancy(int block, int* blocks_per_sm);
+cudaError_t trace_mixed_occupancy(int block, int* blocks_per_sm, bool octree);
 size_t trace_mixed_smem_bytes(int ninstr, int block);
 // out[cell][lambda] (+)= in[lambda][cell]: the absorbed table from the trace's
 // wavelength-major accumulation to the API's cell-major layout
@@ -162,6 +184,12 @@ struct PinnedBuf {
 // error reporting shared by the translation units (api.cu)
 int set_error(int code, const char* fmt, ...);
 
+// api.cu: the common part of grid creation (sizes, bbox, kr in FP32 and FP64,
+// face planes of the nx x ny x nz lattice, events, capture stream)
+int grid_init(skirt_grid_s* g, int nx, int ny, int nz, long long ncell, const double bbox[6], const float* kr);
+int check_bbox(const double* bbox);  // finite, non-empty along every axis
+int check_device();                  // a CUDA device is present
+
 }  // namespace skirt
 
 // The grid handle: the dust densities on the device and the scratch memory
@@ -180,6 +208,10 @@ struct skirt_grid_s {
     skirt::DevBuf cdf;      // dust source: [nlambda][ncell] cumulative distributions
     skirt::DevBuf cdf_aux;  // dust source: tile sums and totals
     skirt::DevBuf abs_lmajor;  // wavelength-major absorbed table of the current call
+    int oct_levels = 0;              // octree grid: finest lattice 2^oct_levels per axis
+    long long oct_nnode = 0;
+    skirt::OctNode* oct_nodes = nullptr;
+    int4* oct_leaf = nullptr;        // per leaf: lattice corner and level
     skirt::PinnedBuf pinned;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaStream_t capture_stream = nullptr;

@@ -13,7 +13,10 @@
 // table, life until a negligible luminosity is left); Sect. 1 (peel-off,
 // continuous absorption, forced scattering); Sect. 5.2 (absorbed table
 // element (cell, wavelength) at cell * N_lambda + wavelength, updated with
-// lock-free atomic additions -- here native FP64 reductions in L2).
+// lock-free atomic additions -- here native FP64 reductions in L2); Sect. 7.9
+// (octree dust grid: a cell crossing steps from a leaf to the leaf across its
+// exit face, through the precomputed face neighbour and a descent by the
+// lattice cell of the entry point).
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -45,7 +48,16 @@ template <> struct P<double> {
     static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000ll); }
 };
 
+// Distance along the ray from o (inverse direction component iv) to the
+// face plane lo + k d.  One fused multiply-add for the plane, so that every
+// grid kind evaluates the same plane to the same value.
 template <typename R>
+__device__ __forceinline__ R face_dist(R lo, int k, R d, R o, R iv)
+{
+    return (fma((R)k, d, lo) - o) * iv;
+}
+
+template <typename R, bool OCT>
 __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -75,6 +87,11 @@ __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A)
     double labs = 0.0;          // L (1 - albedo) (deposit)
     R s_found = 0, last_dusty_end = 0;
     bool found = false;
+    // octree: current leaf (node, level, leaf index, kr); c0..c2 hold its
+    // lattice corner
+    const int OL = A.oct_levels;
+    int onode = 0, olev = 0, oleaf = 0, osteps = 0;
+    float okr = 0.f;
 
     // ---- packet state
     int stage = ST_NEW;
@@ -98,6 +115,26 @@ __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A)
     double l_emit = 0.0, l_abs = 0.0, l_esc = 0.0, l_res = 0.0;
     unsigned long long c_scat = 0, c_dep = 0, c_loc = 0, c_peel = 0;
 
+    // octree: the leaf holding lattice cell (j0, j1, j2), found by descending
+    // from `node` (a node of level `lev`, or a leaf)
+    auto oct_enter = [&](int node, int lev, int j0, int j1, int j2) {
+        int r = __ldg(&A.oct_nodes[node].ref);
+        while (r >= 0 && lev < OL) {
+            ++lev;
+            const int b = OL - lev;
+            node = r + (((j0 >> b) & 1) | (((j1 >> b) & 1) << 1) | (((j2 >> b) & 1) << 2));
+            r = __ldg(&A.oct_nodes[node].ref);
+        }
+        onode = node;
+        olev = oct_leaf_level(r);
+        oleaf = oct_leaf_index(r);
+        okr = __ldg(&A.oct_nodes[node].kr);
+        const int mask = ~((1 << (OL - olev)) - 1);
+        c0 = j0 & mask;
+        c1 = j1 & mask;
+        c2 = j2 & mask;
+    };
+
     auto begin = [&](int m, R ox, R oy, R oz, R vx, R vy, R vz) {
         mode = m;
         o0 = ox; o1 = oy; o2 = oz;
@@ -105,15 +142,21 @@ __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A)
         c0 = cell_index<R>(ox, lo0, d0, nx);
         c1 = cell_index<R>(oy, lo1, d1, ny);
         c2 = cell_index<R>(oz, lo2, d2, nz);
-        if (vx > (R)0) { s0 = 1; iv0 = (R)1 / vx; tn0 = (lo0 + (R)(c0 + 1) * d0 - ox) * iv0; }
-        else if (vx < (R)0) { s0 = -1; iv0 = (R)1 / vx; tn0 = (lo0 + (R)c0 * d0 - ox) * iv0; }
-        else { s0 = 0; iv0 = 0; tn0 = INF; }
-        if (vy > (R)0) { s1 = 1; iv1 = (R)1 / vy; tn1 = (lo1 + (R)(c1 + 1) * d1 - oy) * iv1; }
-        else if (vy < (R)0) { s1 = -1; iv1 = (R)1 / vy; tn1 = (lo1 + (R)c1 * d1 - oy) * iv1; }
-        else { s1 = 0; iv1 = 0; tn1 = INF; }
-        if (vz > (R)0) { s2 = 1; iv2 = (R)1 / vz; tn2 = (lo2 + (R)(c2 + 1) * d2 - oz) * iv2; }
-        else if (vz < (R)0) { s2 = -1; iv2 = (R)1 / vz; tn2 = (lo2 + (R)c2 * d2 - oz) * iv2; }
-        else { s2 = 0; iv2 = 0; tn2 = INF; }
+        if (OCT) {
+            oct_enter(0, 0, c0, c1, c2);
+            osteps = 0;
+        }
+        s0 = vx > (R)0 ? 1 : (vx < (R)0 ? -1 : 0);
+        s1 = vy > (R)0 ? 1 : (vy < (R)0 ? -1 : 0);
+        s2 = vz > (R)0 ? 1 : (vz < (R)0 ? -1 : 0);
+        iv0 = s0 ? (R)1 / vx : (R)0;
+        iv1 = s1 ? (R)1 / vy : (R)0;
+        iv2 = s2 ? (R)1 / vz : (R)0;
+        if (!OCT) {
+            tn0 = s0 ? face_dist<R>(lo0, c0 + (s0 > 0), d0, ox, iv0) : INF;
+            tn1 = s1 ? face_dist<R>(lo1, c1 + (s1 > 0), d1, oy, iv1) : INF;
+            tn2 = s2 ? face_dist<R>(lo2, c2 + (s2 > 0), d2, oz, iv2) : INF;
+        }
         tcur = (R)0;
         tau = 0.0;
     };
@@ -136,12 +179,20 @@ __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A)
     for (;;) {
         if (mode != M_NONE) {
             // ---------------- one cell crossing ----------------
+            int osz = 1;
+            if (OCT) {
+                // exit distances from the current leaf's box
+                osz = 1 << (OL - olev);
+                tn0 = s0 ? face_dist<R>(lo0, c0 + (s0 > 0 ? osz : 0), d0, o0, iv0) : INF;
+                tn1 = s1 ? face_dist<R>(lo1, c1 + (s1 > 0 ? osz : 0), d1, o1, iv1) : INF;
+                tn2 = s2 ? face_dist<R>(lo2, c2 + (s2 > 0 ? osz : 0), d2, o2, iv2) : INF;
+            }
             const int axis = (tn0 <= tn1) ? ((tn0 <= tn2) ? 0 : 2) : ((tn1 <= tn2) ? 1 : 2);
             const R tnext = axis == 0 ? tn0 : (axis == 1 ? tn1 : tn2);
             R ds = tnext - tcur;
             if (ds < (R)0) ds = (R)0;
-            const int m = (c2 * ny + c1) * nx + c0;
-            const R krl = P<R>::kr(A, m) * krs;
+            const int m = OCT ? oleaf : (c2 * ny + c1) * nx + c0;
+            const R krl = (OCT ? (R)okr : P<R>::kr(A, m)) * krs;
             const R dtau_r = krl * ds;
             const double dtau = (double)dtau_r;
             bool done = false;
@@ -169,20 +220,51 @@ __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A)
                 ++c_peel;
                 tau += dtau;
             }
-            if (!done) {
+            if (!done && OCT) {
+                tcur = tnext;
+                const int sa = axis == 0 ? s0 : (axis == 1 ? s1 : s2);
+                const int nb = __ldg(&A.oct_nodes[onode].nb[2 * axis + (sa > 0)]);
+                if (nb < 0) {
+                    done = true;  // the exit face lies on the root box
+                } else if (++osteps > A.oct_step_cap) {
+                    atomicOr(A.err, (unsigned)ERRBIT_PATH);
+                    done = true;
+                } else {
+                    // lattice cell of the entry point into the next leaf: across
+                    // the exit face along `axis`; along the other axes the
+                    // cell of the crossing point, kept within the current
+                    // leaf's cross-section
+                    int j[3];
+                    const int cc[3] = {c0, c1, c2};
+                    const R oo[3] = {o0, o1, o2}, vv[3] = {v0, v1, v2}, ll[3] = {lo0, lo1, lo2},
+                            dd[3] = {d0, d1, d2};
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        if (b == axis) {
+                            j[b] = sa > 0 ? cc[b] + osz : cc[b] - 1;
+                        } else {
+                            const R f = P<R>::floorr((oo[b] + tnext * vv[b] - ll[b]) / dd[b]);
+                            const int jb = f < (R)cc[b] ? cc[b] : (f > (R)(cc[b] + osz - 1) ? cc[b] + osz - 1 : (int)f);
+                            j[b] = jb;
+                        }
+                    }
+                    // a neighbour that is not a leaf has the current level
+                    oct_enter(nb, olev, j[0], j[1], j[2]);
+                }
+            } else if (!done) {
                 tcur = tnext;
                 if (axis == 0) {
                     c0 += s0;
                     if ((unsigned)c0 >= (unsigned)nx) done = true;
-                    else tn0 = (lo0 + (R)(c0 + (s0 > 0)) * d0 - o0) * iv0;
+                    else tn0 = face_dist<R>(lo0, c0 + (s0 > 0), d0, o0, iv0);
                 } else if (axis == 1) {
                     c1 += s1;
                     if ((unsigned)c1 >= (unsigned)ny) done = true;
-                    else tn1 = (lo1 + (R)(c1 + (s1 > 0)) * d1 - o1) * iv1;
+                    else tn1 = face_dist<R>(lo1, c1 + (s1 > 0), d1, o1, iv1);
                 } else {
                     c2 += s2;
                     if ((unsigned)c2 >= (unsigned)nz) done = true;
-                    else tn2 = (lo2 + (R)(c2 + (s2 > 0)) * d2 - o2) * iv2;
+                    else tn2 = face_dist<R>(lo2, c2 + (s2 > 0), d2, o2, iv2);
                 }
             }
             if (done) mode = M_NONE;
@@ -267,7 +349,7 @@ __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A)
                 }
             } else if (A.src_kind == SKIRT_SRC_DUST) {
                 const uint4 r = draw(0u, 0u);
-                const long long ncell = (long long)nx * ny * nz;
+                const long long ncell = A.ncell;
                 const double* cdf = A.cdf + (size_t)lam * ncell;
                 const double u0 = (double)u01f(r.x);
                 long long a = 0, b = ncell - 1;  // first cell with cdf > u0
@@ -275,10 +357,19 @@ __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A)
                     const long long mid = (a + b) >> 1;
                     if (__ldg(cdf + mid) > u0) b = mid; else a = mid + 1;
                 }
-                const int ix = (int)(a % nx), iy = (int)((a / nx) % ny), iz = (int)(a / ((long long)nx * ny));
-                x0 = lo0 + ((R)ix + P<R>::u(r.y)) * d0;
-                x1 = lo1 + ((R)iy + P<R>::u(r.z)) * d1;
-                x2 = lo2 + ((R)iz + P<R>::u(r.w)) * d2;
+                if (OCT) {
+                    // uniform point in the leaf's box
+                    const int4 lf = __ldg(&A.oct_leaf[a]);
+                    const R side = (R)(1 << (OL - lf.w));
+                    x0 = lo0 + ((R)lf.x + P<R>::u(r.y) * side) * d0;
+                    x1 = lo1 + ((R)lf.y + P<R>::u(r.z) * side) * d1;
+                    x2 = lo2 + ((R)lf.z + P<R>::u(r.w) * side) * d2;
+                } else {
+                    const int ix = (int)(a % nx), iy = (int)((a / nx) % ny), iz = (int)(a / ((long long)nx * ny));
+                    x0 = lo0 + ((R)ix + P<R>::u(r.y)) * d0;
+                    x1 = lo1 + ((R)iy + P<R>::u(r.z)) * d1;
+                    x2 = lo2 + ((R)iz + P<R>::u(r.w)) * d2;
+                }
             } else {
                 x0 = (R)A.src_pos[0]; x1 = (R)A.src_pos[1]; x2 = (R)A.src_pos[2];
             }
@@ -482,15 +573,19 @@ cudaError_t launch_trace(const TraceArgs& a, int precision, int block, int grid,
 {
     if (precision == SKIRT_PREC_MIXED) return launch_trace_mixed(a, block, grid, s);
     const size_t smem = trace_smem_bytes(a.ninstr, block);
-    trace_kernel<double><<<grid, block, smem, s>>>(a);
+    if (a.oct_levels > 0)
+        trace_kernel<double, true><<<grid, block, smem, s>>>(a);
+    else
+        trace_kernel<double, false><<<grid, block, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t trace_occupancy(int precision, int block, int* blocks_per_sm)
+cudaError_t trace_occupancy(int precision, int block, int* blocks_per_sm, bool octree)
 {
-    if (precision == SKIRT_PREC_MIXED) return trace_mixed_occupancy(block, blocks_per_sm);
+    if (precision == SKIRT_PREC_MIXED) return trace_mixed_occupancy(block, blocks_per_sm, octree);
     const size_t smem = trace_smem_bytes(16, block);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<double>, block, smem);
+    return octree ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<double, true>, block, smem)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<double, false>, block, smem);
 }
 
 namespace {

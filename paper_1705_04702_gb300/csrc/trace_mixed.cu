@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                     }
                 } else {  // SKIRT_SRC_DUST
                     const uint4 r = draw(0u, 0u);
-                    const long long ncell = (long long)nx * ny * nz;
+                    const long long ncell = A.ncell;
                     const double* cdf = A.cdf + (size_t)lam * ncell;
                     const double u0 = f2d(u01f(r.x));
                     long long a = 0, b = ncell - 1;  // first cell with cdf > u0
@@ -639,8 +639,9 @@ cudaError_t launch_trace_mixed(const TraceArgs& a, int block, int grid, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t trace_mixed_occupancy(int block, int* blocks_per_sm)
+cudaError_t trace_mixed_occupancy(int block, int* blocks_per_sm, bool octree)
 {
+    (void)octree;
     if (block > MAXB || block % 32) {
         *blocks_per_sm = 0;
         return cudaSuccess;

@@ -71,6 +71,8 @@ def _load():
     L.skirt_trace_opts_default.restype = i
     L.skirt_grid_create.argtypes = [ctypes.POINTER(vp), i, i, i, _dp, vp]
     L.skirt_grid_create.restype = i
+    L.skirt_octree_create.argtypes = [ctypes.POINTER(vp), i, _dp, ctypes.c_longlong, vp, vp]
+    L.skirt_octree_create.restype = i
     L.skirt_grid_destroy.argtypes = [vp]
     L.skirt_grid_destroy.restype = i
     L.skirt_trace.argtypes = [vp, ctypes.POINTER(skirt_source), ctypes.POINTER(skirt_wavelengths),
@@ -128,6 +130,17 @@ def skirt_grid_create(nx, ny, nz, bbox, kr):
     h = ctypes.c_void_p()
     bb = (ctypes.c_double * 6)(*[float(v) for v in bbox])
     _check(lib.skirt_grid_create(ctypes.byref(h), int(nx), int(ny), int(nz), bb, _ptr(kr)), "skirt_grid_create")
+    return h
+
+
+def skirt_octree_create(max_level, bbox, leaves, kr):
+    """leaves: int32 numpy array [nleaf, 4] (level, ix, iy, iz); kr: float32
+    torch tensor (CUDA or CPU) or numpy array of nleaf values."""
+    h = ctypes.c_void_p()
+    bb = (ctypes.c_double * 6)(*[float(v) for v in bbox])
+    lv = np.ascontiguousarray(leaves, dtype=np.int32)
+    _check(lib.skirt_octree_create(ctypes.byref(h), int(max_level), bb, int(lv.shape[0]), _ptr(lv), _ptr(kr)),
+           "skirt_octree_create")
     return h
 
 
@@ -200,16 +213,20 @@ def make_instruments(instruments):
 
 class Grid:
     """Owns a skirt grid handle built from a workloads.Grid (or any object with
-    nx, ny, nz, bbox, kr)."""
+    nx, ny, nz, bbox, kr) or a workloads.Octree (max_level, bbox, leaves, kr)."""
 
     def __init__(self, grid, kr=None):
         import torch
         self.nx, self.ny, self.nz = grid.nx, grid.ny, grid.nz
         self.bbox = tuple(grid.bbox)
-        self.ncell = grid.nx * grid.ny * grid.nz
+        self.octree = getattr(grid, "leaves", None) is not None
+        self.ncell = grid.ncell if self.octree else grid.nx * grid.ny * grid.nz
         if kr is None:
             kr = torch.from_numpy(np.ascontiguousarray(grid.kr, dtype=np.float32).ravel())
-        self.h = skirt_grid_create(self.nx, self.ny, self.nz, self.bbox, kr)
+        if self.octree:
+            self.h = skirt_octree_create(grid.max_level, self.bbox, grid.leaves, kr)
+        else:
+            self.h = skirt_grid_create(self.nx, self.ny, self.nz, self.bbox, kr)
 
     def close(self):
         if self.h is not None and self.h.value:

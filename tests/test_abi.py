@@ -83,3 +83,42 @@ def test_emission_grid_matches_the_oracle(skirt):
     lam2, W2 = E.emission_grid()
     np.testing.assert_allclose(lam, lam2, rtol=1e-14)
     np.testing.assert_allclose(W, W2, rtol=1e-13)
+
+
+def test_octree_leaves_are_validated_on_the_host(skirt):
+    """Malformed leaf lists are refused before any device work: holes,
+    overlaps, positions outside a level's range, levels beyond max_level."""
+    from paper_1705_04702_gb300 import workloads as W
+    lib = skirt.lib
+    bb = (ctypes.c_double * 6)(-1, 1, -1, 1, -1, 1)
+    tree = W.refine_octree(lambda x, y, z: 1.0 + 50.0 * np.exp(-(x * x + y * y + z * z) / 0.02),
+                           (-1, 1, -1, 1, -1, 1), 4, 1, 1e-2)
+    kr = np.ones(tree.ncell + 1, dtype=np.float32)
+
+    def create(leaves, max_level=tree.max_level):
+        lv = np.ascontiguousarray(leaves, dtype=np.int32)
+        h = ctypes.c_void_p()
+        return lib.skirt_octree_create(ctypes.byref(h), max_level, bb, lv.shape[0], lv.ctypes.data_as(ctypes.c_void_p),
+                                       kr.ctypes.data_as(ctypes.c_void_p)), lib.skirt_last_error()
+
+    code, msg = create(tree.leaves[1:])
+    assert code == skirt.ERR_INVALID_ARG and b"hole" in msg
+    code, msg = create(np.concatenate([tree.leaves, tree.leaves[3:4]]))
+    assert code == skirt.ERR_INVALID_ARG and b"overlaps" in msg
+    parent = tree.leaves[tree.leaves[:, 0] == tree.max_level][:1].copy()
+    parent[0, 0] -= 1
+    parent[0, 1:] //= 2
+    code, msg = create(np.concatenate([tree.leaves, parent]))
+    assert code == skirt.ERR_INVALID_ARG and (b"overlaps" in msg or b"inside" in msg)
+    bad = tree.leaves.copy()
+    bad[5, 2] = 1 << int(bad[5, 0])
+    code, msg = create(bad)
+    assert code == skirt.ERR_INVALID_ARG and b"leaf 5" in msg
+    code, _ = create(tree.leaves, max_level=tree.max_level - 1)
+    assert code == skirt.ERR_INVALID_ARG
+    code, _ = create(tree.leaves, max_level=16)
+    assert code == skirt.ERR_INVALID_ARG
+    import torch
+    if not torch.cuda.is_available():
+        code, _ = create(tree.leaves)
+        assert code == skirt.ERR_NO_DEVICE
