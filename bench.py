@@ -44,17 +44,23 @@ def parse():
     ap.add_argument("--packets", type=float, default=1e8)
     ap.add_argument("--grid", type=int, default=256)
     ap.add_argument("--fp64-packets", type=float, default=1e7)
-    ap.add_argument("--cpu-packets", type=int, default=60000)
+    ap.add_argument("--cpu-packets", type=int, default=None,
+                    help="oracle sample per core (default 60000; 2000 on the octree, whose oracle lists "
+                         "every finest-lattice plane)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--epochs", type=int, default=60, help="learned workload: training epochs")
     ap.add_argument("--lr", type=float, default=2e-3, help="learned workload: Adam step size")
-    ap.add_argument("--workload", default="disk", choices=["disk", "disk40", "torus", "learned", "selfabs"],
+    ap.add_argument("--workload", default="disk", choices=["disk", "disk40", "torus", "octree", "learned", "selfabs"],
                     help="disk: 1 wavelength, --packets packets (default); disk40: 40 wavelengths, "
                          "--packets per wavelength; torus: clumpy torus, 200 wavelengths, uneven counts "
-                         "(--packets scales them, 1e8 = the full 7.5e8-packet run)")
-    return ap.parse_args()
+                         "(--packets scales them, 1e8 = the full 7.5e8-packet run); octree: the disk galaxy "
+                         "on an 8.25M-leaf octree, 1 wavelength, --packets packets")
+    a = ap.parse_args()
+    if a.cpu_packets is None:
+        a.cpu_packets = 2000 if a.workload == "octree" else 60000
+    return a
 
 
 def peaks():
@@ -72,6 +78,8 @@ def workload(args):
         return W.disk_problem(int(args.packets), n=args.grid, nlambda=40, npx=512)
     if args.workload == "torus":
         return W.torus_problem(n=args.grid, nlambda=200, npx=512, packet_scale=args.packets / 1e8)
+    if args.workload == "octree":
+        return W.octree_problem(W.disk_octree(), int(args.packets), npx=512)
     return W.disk_problem(int(args.packets), n=args.grid, nlambda=1, npx=512)
 
 
@@ -83,6 +91,11 @@ def workload_name(args, prob):
         return (f"clumpy two-phase dust torus, {args.grid}^3 Cartesian grid, 200 wavelengths 0.09-10 um, "
                 f"{prob.total_packets:.3e} packets (1e5-2e7 per wavelength, log-uniform), "
                 f"3 instruments 512x512 (i=0/60/90)")
+    if args.workload == "octree":
+        lv = prob.grid.leaves[:, 0]
+        return (f"exponential-disk galaxy on an octree dust grid over [-24,24]^3: {prob.grid.ncell} leaves "
+                f"(levels {lv.min()}-{lv.max()}, at most {prob.grid.max_level}), 1 wavelength (0.55 um), "
+                f"{int(args.packets):.0e} packets, 3 instruments 512x512 (i=0/60/90)")
     return (f"exponential-disk galaxy, {args.grid}^3 Cartesian grid, 1 wavelength (0.55 um), "
             f"{int(args.packets):.0e} packets, 3 instruments 512x512 (i=0/60/90)")
 
@@ -90,7 +103,7 @@ def workload_name(args, prob):
 def config_of(args, prob, extra=None):
     c = {
         "workload": workload_name(args, prob),
-        "grid": args.grid,
+        "grid": f"octree, {prob.grid.ncell} leaves" if args.workload == "octree" else args.grid,
         "nlambda": prob.wl.n,
         "packets_per_step": prob.total_packets,
         "instruments": len(prob.instruments),
@@ -217,7 +230,7 @@ def run_reference(args):
         return
     prob = workload(args)
     pool = OraclePool(args)
-    per_core = max(1, min(20000, int(args.packets) // max(pool.cores * (args.warmup + args.steps), 1)))
+    per_core = max(1, min(args.cpu_packets // 3, int(args.packets) // max(pool.cores * (args.warmup + args.steps), 1)))
     lo = 0
     for _ in range(args.warmup):
         pool.step(lo, per_core)
@@ -432,8 +445,11 @@ def main():
     packets = prob.total_packets
     value = job_throughput(packets, world, args.steps, elapsed)
 
-    # ---- roofline of the trace kernel: algorithmic bytes per launch
-    kr_b = 4
+    # ---- roofline of the trace kernel: algorithmic bytes per launch (per
+    # crossing the cell's kr; on the octree the next leaf's node head, 8 B,
+    # and the face-neighbour index, 4 B)
+    octree = args.workload == "octree"
+    kr_b = 12 if octree else 4
     per_launch_bytes = (kr_b * (led["deposit_steps"] + led["locate_steps"] + led["peel_steps"])
                         + 16 * led["deposit_steps"]
                         + 16 * (packets + led["scatterings"]) * len(prob.instruments))
@@ -445,7 +461,8 @@ def main():
     # the packets of this launch; None for other workloads
     traffic = 30251.5 * packets if (args.workload == "disk" and args.grid == 256) else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "peak_source": peak_kind, "kernel": "trace_mixed_kernel",
+            "traffic": traffic, "peak_source": peak_kind,
+            "kernel": "trace_mixed_kernel<true> (octree)" if octree else "trace_mixed_kernel",
             "kernel_ms": k_ms, "algorithmic_bytes_per_launch": per_launch_bytes,
             "per_packet": {"deposit_steps": led["deposit_steps"] / packets,
                            "locate_steps": led["locate_steps"] / packets,
@@ -505,6 +522,12 @@ def main():
         dte = (time.perf_counter() - t0) / ksteps
         h2d = h_kr.numel() * 4
         d2h = (h_abs.numel() + h_img.numel() + h_sed.numel()) * 8
+        if octree:
+            # grid creation uploads the node array (32 B per node, 1 + 8 (nleaf - 1) / 7 nodes), the
+            # leaf table (16 B) and the leaf-to-node map (4 B), and reads kr back once (4 B per leaf)
+            nl = prob.grid.ncell
+            h2d += 32 * (1 + 8 * (nl - 1) // 7) + 20 * nl
+            d2h += 4 * nl
         e2e = {"value": packets * world / dte, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": ksteps}
 

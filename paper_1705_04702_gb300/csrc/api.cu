@@ -346,8 +346,6 @@ int validate(skirt_grid_t g, const skirt_source* src, const skirt_wavelengths* w
     if (src->kind == SKIRT_SRC_DUST && !src->emission) return fail(SKIRT_ERR_INVALID_ARG, "dust source needs emission");
     if (opts->precision != SKIRT_PREC_FP64 && opts->precision != SKIRT_PREC_MIXED)
         return fail(SKIRT_ERR_INVALID_ARG, "unknown precision %d", opts->precision);
-    if (g->oct_levels > 0 && opts->precision != SKIRT_PREC_FP64)
-        return fail(SKIRT_ERR_INVALID_ARG, "octree grids are traced in the FP64 form");
     if (opts->schedule != SKIRT_SCHED_PER_LAMBDA && opts->schedule != SKIRT_SCHED_PERSISTENT)
         return fail(SKIRT_ERR_INVALID_ARG, "unknown schedule %d", opts->schedule);
     if (opts->block != 0 && (opts->block < 32 || opts->block % 32 ||

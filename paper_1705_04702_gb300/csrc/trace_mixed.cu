@@ -134,7 +134,11 @@ struct Cold {
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
+// OCT: octree grid (Sect. 7.9).  The traversal state then names a leaf
+// (node, level, lattice corner) instead of a cell; a crossing reads the face
+// neighbour and descends from it by the lattice cell of the entry point.
+template <bool OCT>
+__global__ void __launch_bounds__(MAXB, OCT ? 2 : 3) trace_mixed_kernel(const TraceArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     InstrDev* sins = reinterpret_cast<InstrDev*>(smem);
@@ -177,6 +181,13 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
     int cur_m = 0;       // index of the current cell
     float kr_cur = 0.f;  // its extinction coefficient (loaded one crossing ahead)
     const int nxy = nx * ny;
+    // octree: the current leaf's node and level (c0..c2: its lattice corner),
+    // the traversal direction, the node of the interaction leaf
+    const int OL = A.oct_levels;
+    const OctNode* __restrict__ nodes = A.oct_nodes;
+    const float id0 = 1.f / d0, id1 = 1.f / d1, id2 = 1.f / d2;
+    int onode = 0, olev = 0, pc_node = 0;
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f;
     // ---- packet state (registers)
     int stage = ST_NEW;
     bool alive = true;
@@ -194,6 +205,26 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
         return c;
     };
 
+    // octree: enter the leaf holding lattice cell (j0, j1, j2), descending
+    // from `node` (a leaf, or a node of level `lev`)
+    auto oct_enter = [&](int node, int lev, int j0, int j1, int j2) {
+        int2 h = __ldg(reinterpret_cast<const int2*>(nodes + node));
+        while (h.x >= 0 && lev < OL) {
+            ++lev;
+            const int b = OL - lev;
+            node = h.x + (((j0 >> b) & 1) | (((j1 >> b) & 1) << 1) | (((j2 >> b) & 1) << 2));
+            h = __ldg(reinterpret_cast<const int2*>(nodes + node));
+        }
+        onode = node;
+        olev = oct_leaf_level(h.x);
+        cur_m = oct_leaf_index(h.x);
+        kr_cur = __int_as_float(h.y);
+        const int mask = ~((1 << (OL - olev)) - 1);
+        c0 = j0 & mask;
+        c1 = j1 & mask;
+        c2 = j2 & mask;
+    };
+
     auto begin = [&](int m, float vx, float vy, float vz) {
         mode = m;
         const float l0 = C.xl0[t], l1 = C.xl1[t], l2 = C.xl2[t];
@@ -204,6 +235,11 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
             c1 = axis_cell(x1, l1, lo1, d1, ny, fy);
             c2 = axis_cell(x2, l2, lo2, d2, nz, fz);
         }
+        if constexpr (OCT) {
+            if (have_pc) oct_enter(pc_node, 0, c0, c1, c2);
+            else oct_enter(0, 0, c0, c1, c2);
+            v0 = vx; v1 = vy; v2 = vz;
+        }
         s0 = vx > 0.f ? 1 : (vx < 0.f ? -1 : 0);
         s1 = vy > 0.f ? 1 : (vy < 0.f ? -1 : 0);
         s2 = vz > 0.f ? 1 : (vz < 0.f ? -1 : 0);
@@ -211,15 +247,97 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
         iv1 = s1 ? 1.f / vy : 0.f;
         iv2 = s2 ? 1.f / vz : 0.f;
         // first faces from the exact face planes and the double-float position
-        tn0 = s0 ? df_diff(__ldg(fx + c0 + (s0 > 0)), x0, l0) * iv0 : INF;
-        tn1 = s1 ? df_diff(__ldg(fy + c1 + (s1 > 0)), x1, l1) * iv1 : INF;
-        tn2 = s2 ? df_diff(__ldg(fz + c2 + (s2 > 0)), x2, l2) * iv2 : INF;
+        const int e = OCT ? 1 << (OL - olev) : 1;  // the cell's extent in lattice cells
+        tn0 = s0 ? df_diff(__ldg(fx + c0 + (s0 > 0 ? e : 0)), x0, l0) * iv0 : INF;
+        tn1 = s1 ? df_diff(__ldg(fy + c1 + (s1 > 0 ? e : 0)), x1, l1) * iv1 : INF;
+        tn2 = s2 ? df_diff(__ldg(fz + c2 + (s2 > 0 ? e : 0)), x2, l2) * iv2 : INF;
         tcur = 0.f;
         tau_h = tau_l = 0.f;
         nsteps = 0;
         last_axis = -1;
-        cur_m = (c2 * ny + c1) * nx + c0;
-        kr_cur = __ldg(kr + cur_m);
+        if constexpr (!OCT) {
+            cur_m = (c2 * ny + c1) * nx + c0;
+            kr_cur = __ldg(kr + cur_m);
+        }
+    };
+
+    // one leaf crossing of an octree traversal: the face neighbour and its
+    // node are loaded before the crossing's work
+    auto step_oct = [&]() {
+        const float tmin = fminf(fminf(tn0, tn1), tn2);
+        const int axis = (tn0 == tmin) ? 0 : ((tn1 == tmin) ? 1 : 2);
+        const int ss = axis == 0 ? s0 : (axis == 1 ? s1 : s2);
+        const int nb = __ldg(&nodes[onode].nb[2 * axis + (ss > 0)]);
+        const bool out = nb < 0;
+        const int2 nbh = out ? make_int2(0, 0) : __ldg(reinterpret_cast<const int2*>(nodes + nb));
+        const float ds = fmaxf(tmin - tcur, 0.f);
+        const int m = cur_m;
+        const float krl = kr_cur * krs;
+        const float dtau = krl * ds;
+        ++nsteps;
+        bool done = false;
+        const float tau_prev = tau_h + tau_l;
+        if (mode == M_LOCATE) {
+            if (krl > 0.f) {
+                if (tau_h + (tau_l + dtau) >= rem_f) {
+                    s_found = (rem_f - tau_prev) / krl;
+                    found = true;
+                    done = true;
+                } else {
+                    last_dusty_end = tmin;
+                }
+            }
+        } else if (mode == M_DEPOSIT && dtau > 0.f) {
+            const float dep = labs_f * exp_neg(tau_prev) * one_minus_exp_neg(dtau);
+            if (dep >= 1.17549435e-38f)
+                atomicAdd(absorbed + ((size_t)m * A.abs_cs + (size_t)lam * A.abs_ls), f2d_pos(dep));
+        }
+        df_accumulate(tau_h, tau_l, dtau);
+        if (!done) {
+            tcur = tmin;
+            if (out) {
+                done = true;
+            } else if (nsteps > (unsigned)A.oct_step_cap) {
+                atomicOr(A.err, (unsigned)ERRBIT_PATH);
+                done = true;
+            } else {
+                // lattice cell of the entry point: across the exit face along
+                // `axis`, elsewhere the crossing point's cell kept within the
+                // current leaf's cross-section
+                const int e = 1 << (OL - olev);
+                const float p0 = floorf((x0 + tmin * v0 - lo0) * id0);
+                const float p1 = floorf((x1 + tmin * v1 - lo1) * id1);
+                const float p2 = floorf((x2 + tmin * v2 - lo2) * id2);
+                int j0 = (int)fminf(fmaxf(p0, (float)c0), (float)(c0 + e - 1));
+                int j1 = (int)fminf(fmaxf(p1, (float)c1), (float)(c1 + e - 1));
+                int j2 = (int)fminf(fmaxf(p2, (float)c2), (float)(c2 + e - 1));
+                const int ja = ss > 0 ? (axis == 0 ? c0 : (axis == 1 ? c1 : c2)) + e
+                                      : (axis == 0 ? c0 : (axis == 1 ? c1 : c2)) - 1;
+                j0 = axis == 0 ? ja : j0;
+                j1 = axis == 1 ? ja : j1;
+                j2 = axis == 2 ? ja : j2;
+                // a neighbour that is not a leaf has the current level
+                if (nbh.x < 0) {
+                    onode = nb;
+                    olev = oct_leaf_level(nbh.x);
+                    cur_m = oct_leaf_index(nbh.x);
+                    kr_cur = __int_as_float(nbh.y);
+                    const int mask = ~((1 << (OL - olev)) - 1);
+                    c0 = j0 & mask;
+                    c1 = j1 & mask;
+                    c2 = j2 & mask;
+                } else {
+                    oct_enter(nb, olev, j0, j1, j2);
+                }
+                const int en = 1 << (OL - olev);
+                tn0 = s0 ? (lo0 + (float)(c0 + (s0 > 0 ? en : 0)) * d0 - x0) * iv0 : INF;
+                tn1 = s1 ? (lo1 + (float)(c1 + (s1 > 0 ? en : 0)) * d1 - x1) * iv1 : INF;
+                tn2 = s2 ? (lo2 + (float)(c2 + (s2 > 0 ? en : 0)) * d2 - x2) * iv2 : INF;
+                last_axis = axis;
+            }
+        }
+        if (tau_h > TAU_CUT && mode != M_LOCATE) done = true;
+        if (done) mode = M_NONE;
     };
 
     // one cell crossing of the current traversal
@@ -414,17 +532,26 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                         const long long mid = (a + b) >> 1;
                         if (__ldg(cdf + mid) > u0) b = mid; else a = mid + 1;
                     }
-                    pc0 = (int)(a % nx);
-                    pc1 = (int)((a / nx) % ny);
-                    pc2 = (int)(a / ((long long)nx * ny));
+                    float side = 1.f;  // the cell's extent in lattice cells
+                    if constexpr (OCT) {
+                        // uniform point in the leaf's box; its leaf is found again
+                        // from the position
+                        const int4 lf = __ldg(&A.oct_leaf[a]);
+                        pc0 = lf.x; pc1 = lf.y; pc2 = lf.z;
+                        side = (float)(1 << (OL - lf.w));
+                    } else {
+                        pc0 = (int)(a % nx);
+                        pc1 = (int)((a / nx) % ny);
+                        pc2 = (int)(a / ((long long)nx * ny));
+                    }
                     const float2 f0 = __ldg(fx + pc0), f1 = __ldg(fy + pc1), f2 = __ldg(fz + pc2);
                     x0 = f0.x; l0 = f0.y;
                     x1 = f1.x; l1 = f1.y;
                     x2 = f2.x; l2 = f2.y;
-                    df_add_prod(x0, l0, u01f(r.y), d0);
-                    df_add_prod(x1, l1, u01f(r.z), d1);
-                    df_add_prod(x2, l2, u01f(r.w), d2);
-                    have_pc = true;
+                    df_add_prod(x0, l0, u01f(r.y), side * d0);
+                    df_add_prod(x1, l1, u01f(r.z), side * d1);
+                    df_add_prod(x2, l2, u01f(r.w), side * d2);
+                    have_pc = !OCT;
                 }
                 C.xl0[t] = l0; C.xl1[t] = l1; C.xl2[t] = l2;
                 if (isotropic) {
@@ -493,9 +620,10 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                     df_add_prod(x0, l0, tcur, k0);
                     df_add_prod(x1, l1, tcur, k1);
                     df_add_prod(x2, l2, tcur, k2);
-                    if (last_axis == 0) { const float2 f = __ldg(fx + c0 + (s0 < 0)); x0 = f.x; l0 = f.y; }
-                    else if (last_axis == 1) { const float2 f = __ldg(fy + c1 + (s1 < 0)); x1 = f.x; l1 = f.y; }
-                    else { const float2 f = __ldg(fz + c2 + (s2 < 0)); x2 = f.x; l2 = f.y; }
+                    const int e = OCT ? 1 << (OL - olev) : 1;
+                    if (last_axis == 0) { const float2 f = __ldg(fx + c0 + (s0 < 0 ? e : 0)); x0 = f.x; l0 = f.y; }
+                    else if (last_axis == 1) { const float2 f = __ldg(fy + c1 + (s1 < 0 ? e : 0)); x1 = f.x; l1 = f.y; }
+                    else { const float2 f = __ldg(fz + c2 + (s2 < 0 ? e : 0)); x2 = f.x; l2 = f.y; }
                     df_add_prod(x0, l0, s_found, k0);
                     df_add_prod(x1, l1, s_found, k1);
                     df_add_prod(x2, l2, s_found, k2);
@@ -507,7 +635,7 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                 }
                 C.xl0[t] = l0; C.xl1[t] = l1; C.xl2[t] = l2;
                 have_pc = found;
-                if (found) { pc0 = c0; pc1 = c1; pc2 = c2; }
+                if (found) { pc0 = c0; pc1 = c1; pc2 = c2; pc_node = onode; }
                 L = L * C.alb[t] * C.om[t];
                 C.nscat[t] = (int)C.ev[t];
                 if (L > 0.f && A.peel && A.ninstr > 0) {
@@ -602,8 +730,13 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
         if (!(sm | wm)) break;
         if (sm && (__popc(sm) >= step_min || !wm)) {
 #pragma unroll 1
-            for (int r = 0; r < ROUND; ++r)
-                if (mode != M_NONE) step();
+            for (int r = 0; r < ROUND; ++r) {
+                if constexpr (OCT) {
+                    if (mode != M_NONE) step_oct();
+                } else {
+                    if (mode != M_NONE) step();
+                }
+            }
             continue;
         }
         if (!stepping && alive) events();
@@ -626,7 +759,10 @@ size_t trace_mixed_smem_bytes(int ninstr, int block)
 
 static cudaError_t set_smem_limit()
 {
-    return cudaFuncSetAttribute(trace_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(trace_mixed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)trace_mixed_smem_bytes(16, MAXB));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(trace_mixed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)trace_mixed_smem_bytes(16, MAXB));
 }
 
@@ -635,21 +771,25 @@ cudaError_t launch_trace_mixed(const TraceArgs& a, int block, int grid, cudaStre
     if (block > MAXB || block % 32) return cudaErrorInvalidValue;
     cudaError_t e = set_smem_limit();
     if (e != cudaSuccess) return e;
-    trace_mixed_kernel<<<grid, block, trace_mixed_smem_bytes(a.ninstr, block), s>>>(a);
+    if (a.oct_levels > 0)
+        trace_mixed_kernel<true><<<grid, block, trace_mixed_smem_bytes(a.ninstr, block), s>>>(a);
+    else
+        trace_mixed_kernel<false><<<grid, block, trace_mixed_smem_bytes(a.ninstr, block), s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t trace_mixed_occupancy(int block, int* blocks_per_sm, bool octree)
 {
-    (void)octree;
     if (block > MAXB || block % 32) {
         *blocks_per_sm = 0;
         return cudaSuccess;
     }
     cudaError_t e = set_smem_limit();
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_mixed_kernel, block,
-                                                         trace_mixed_smem_bytes(16, block));
+    return octree ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_mixed_kernel<true>, block,
+                                                                  trace_mixed_smem_bytes(16, block))
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_mixed_kernel<false>, block,
+                                                                  trace_mixed_smem_bytes(16, block));
 }
 
 }  // namespace skirt

@@ -112,6 +112,40 @@ def test_torus_256_fp64_histories_follow_the_oracle(S, oracle_lib):
     compare_records(rec, r["records"], small, 1e-7, 0.999, same_n_min=1.0)
 
 
+def test_disk_octree_8m_leaves_sampled(S, oracle_lib):
+    """The ERIS-sized octree: the exponential dust disk refined by dust mass
+    into 8.25M leaves (levels 4 to 11, at most 13 levels), 1e7 packets in the
+    mixed form in one graph launch; the oracle replays the first 1000 packets
+    (its own tree and finest-lattice path listing).  Then the first 300
+    packets in the FP64 form follow the oracle to 1e-9."""
+    from parity import REL_FP64
+    tree = W.disk_octree()
+    assert 8.0e6 < tree.ncell < 8.5e6 and tree.max_level == 13
+    prob = W.octree_problem(tree, 10_000_000, npx=512)
+    grid = S.Grid(tree)
+    g = _check_full_on(S, oracle_lib, prob, grid, 1000, 0.998)
+    assert float(g["absorbed"].min()) >= 0.0
+    small = prob.with_packets(300)
+    g = S.run_problem(small, grid, precision=S.PREC_FP64, nrec=300)
+    r = oracle_lib.trace(small, 0, 300, nrec=300)
+    compare_records(g["records"].cpu().numpy(), r["records"], small, REL_FP64, 1.0, same_n_min=1.0)
+    grid.close()
+
+
+def _check_full_on(S, oracle_lib, prob, grid, nrec, min_match):
+    g = S.run_problem(prob, grid, precision=S.PREC_MIXED, schedule=S.SCHED_PERSISTENT, nrec=nrec, use_graph=True)
+    r = oracle_lib.trace(prob, 0, nrec, nrec=nrec)
+    compare_records(g["records"].cpu().numpy(), r["records"], prob, REL_MIXED_PACKET, min_match, same_n_min=0.999)
+    led = g["ledger"]
+    assert g["status"] == S.OK and led["status_bits"] == 0
+    closure = abs(led["emitted"] - led["absorbed"] - led["escaped"] - led["residual"]) / led["emitted"]
+    assert closure < 1e-6
+    assert float(g["absorbed"].sum()) == pytest.approx(led["absorbed"], rel=1e-6)
+    c = r["counters"] / nrec
+    assert led["scatterings"] / prob.total_packets == pytest.approx(c[0], rel=0.1)
+    return g
+
+
 def test_learned_form_full_grid_sampled(S, oracle_lib):
     """The learned form on the full 256^3 clumpy torus (16.8M cells, 200
     wavelengths; the absorbed table from a 5% stellar trace): band features
