@@ -1,7 +1,8 @@
 /*
  * skirt.h -- C ABI of the GB300 Monte Carlo dust radiative transfer library.
  *
- * The library traces photon packets through a 3-D Cartesian dust grid on one
+ * The library traces photon packets through a 3-D dust grid (Cartesian, or
+ * an adaptive octree as in the paper's Sect. 7.9) on one
  * NVIDIA GB300 (sm_103a) and accumulates the absorbed luminosity per cell and
  * wavelength, per-pixel per-wavelength instrument images and SEDs.  The
  * operations follow the method of Verstocken et al. (arXiv:1705.04702):

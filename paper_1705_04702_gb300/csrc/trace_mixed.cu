@@ -138,7 +138,7 @@ __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(siz
 // (node, level, lattice corner) instead of a cell; a crossing reads the face
 // neighbour and descends from it by the lattice cell of the entry point.
 template <bool OCT>
-__global__ void __launch_bounds__(MAXB, OCT ? 2 : 3) trace_mixed_kernel(const TraceArgs A)
+__global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     InstrDev* sins = reinterpret_cast<InstrDev*>(smem);
