@@ -459,7 +459,10 @@ def main():
     # DRAM bytes (read + write) per packet of trace_mixed_kernel on the 256^3 disk, from one ncu
     # capture of a 3e6-packet launch (profiles/trace_mixed_kernel_disk256_3e6_full.md), scaled by
     # the packets of this launch; None for other workloads
-    traffic = 30251.5 * packets if (args.workload == "disk" and args.grid == 256) else None
+    # (and of trace_mixed_kernel<true> on the 8.25M-leaf octree: 136.0 kB per packet,
+    # profiles/trace_mixed_kernel_octree8m_3e6_full.md)
+    traffic = (30251.5 * packets if (args.workload == "disk" and args.grid == 256) else
+               136005.5 * packets if octree else None)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_source": peak_kind,
             "kernel": "trace_mixed_kernel<true> (octree)" if octree else "trace_mixed_kernel",
