@@ -462,7 +462,7 @@ def main():
     # (and of trace_mixed_kernel<true> on the 8.25M-leaf octree: 136.0 kB per packet,
     # profiles/trace_mixed_kernel_octree8m_3e6_full.md)
     traffic = (30251.5 * packets if (args.workload == "disk" and args.grid == 256) else
-               136005.5 * packets if octree else None)
+               136006.1 * packets if octree else None)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_source": peak_kind,
             "kernel": "trace_mixed_kernel<true> (octree)" if octree else "trace_mixed_kernel",

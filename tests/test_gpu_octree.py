@@ -215,3 +215,38 @@ def test_octree_mixed_uniform_tree_close_to_the_regular_grid_kernel(S):
     b = S.run_problem(tprob, precision=S.PREC_MIXED, nrec=20000)
     compare_records(_np(b["records"]), _np(a["records"]), prob, REL_MIXED_PACKET, 0.999, same_n_min=0.999)
     compare_tally(_np(b["absorbed"]), _np(a["absorbed"]), REL_MIXED_TALLY, significant=MIXED_CELL_SIGNIFICANT)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_octree_self_absorption_cycles(S, oracle_lib, precision):
+    """The dust self-absorption loop on an adaptive grid: stellar absorption
+    of the disk on a tree of levels 2 to 5 (oracle, 6 wavelengths), leaf
+    masses from the leaf boxes, dust extinction raised 2000x so that the dust
+    re-absorbs ~20% of its emission (4 cycles at 1%); cycle count,
+    per-cycle totals and the last dust table against the oracle's loop."""
+    import torch
+    from oracle import selfabsorb as OSA
+    from paper_1705_04702_gb300.selfabsorb import self_absorption
+    tree = W.refine_octree(W.disk_density(), (-24.0, 24.0, -24.0, 24.0, -24.0, 24.0), 5, 2, 2e-3)
+    prob = W.octree_problem(tree, 1500, nlambda=6, npx=16)
+    A = oracle_lib.trace(prob)["absorbed"]
+    a, b = tree.boxes()
+    mass = (tree.kr.astype(np.float64) * np.prod(b - a, axis=1)).astype(np.float32)
+    wl = OSA.dust_wavelengths()
+    wl = dataclasses.replace(wl, kscale=wl.kscale * 2000.0)
+    ref = OSA.self_absorption(tree, A, prob.wl.lam, mass, 300, 5, tol=1e-2, max_cycles=12, wl=wl)
+    assert ref["cycles"] >= 3 and ref["converged"]
+    grid = S.Grid(tree)
+    m_d = torch.empty(tree.ncell, dtype=torch.float32, device="cuda")
+    S.skirt_dust_mass(grid.h, m_d)
+    np.testing.assert_allclose(m_d.cpu().numpy(), mass, rtol=2e-7)
+    out = self_absorption(grid, torch.as_tensor(A, device="cuda"), prob.wl.lam, torch.as_tensor(mass, device="cuda"),
+                          300, 5, tol=1e-2, max_cycles=12, precision=precision, wl=wl)
+    grid.close()
+    assert out["converged"] and out["cycles"] == ref["cycles"]
+    fp64 = precision == 0
+    for g, r in zip(out["history"], ref["history"]):
+        assert g["emitted"] == pytest.approx(r["emitted"], rel=1e-9 if fp64 else 1e-4)
+        assert g["absorbed"] == pytest.approx(r["absorbed"], rel=1e-9 if fp64 else 1e-4)
+    compare_tally(out["absorbed_dust"].cpu().numpy(), ref["absorbed_dust"], 1e-9 if fp64 else REL_MIXED_TALLY,
+                  significant=1e-6 if fp64 else MIXED_CELL_SIGNIFICANT, l1=1e-9 if fp64 else 2e-4)
