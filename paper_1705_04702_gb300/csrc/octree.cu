@@ -68,9 +68,13 @@ extern "C" int skirt_octree_create(skirt_grid_t* out, int max_level, const doubl
     if (!bbox || !leaves || !kr) return set_error(SKIRT_ERR_INVALID_ARG, "bbox / leaves / kr is NULL");
     if (int r = check_bbox(bbox)) return r;
 
-    // ---- insert the leaves from the root down (kind: 0 empty, 1 split, 2 leaf)
-    std::vector<int> ref(1, 0);
-    std::vector<unsigned char> kind(1, 0);
+    // ---- insert the leaves from the root down (kind: 0 empty, 1 split, 2 leaf,
+    // 3 unused).  The root is node 0 and nodes 1..7 stay unused, so that every
+    // block of 8 children starts at a multiple of 8: a node's octant is then
+    // its index mod 8, and its sibling across an axis is index ^ (1 << axis).
+    std::vector<int> ref(8, 0);
+    std::vector<unsigned char> kind(8, 3);
+    kind[0] = 0;
     std::vector<int> leaf_node((size_t)nleaf);
     std::vector<int4> leaf_tab((size_t)nleaf);
     for (long long m = 0; m < nleaf; ++m) {

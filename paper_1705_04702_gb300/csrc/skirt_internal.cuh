@@ -47,7 +47,8 @@ struct InstrDev {
 enum { ERRBIT_EVENT_CAP = 1, ERRBIT_SOURCE = 2, ERRBIT_NONFINITE = 4, ERRBIT_PATH = 8 };
 
 // Octree node (32 bytes, one sector).  ref >= 0: internal node whose 8
-// children are nodes ref .. ref+7 (octant x + 2y + 4z); ref < 0: a leaf,
+// children are nodes ref .. ref+7 (octant x + 2y + 4z; ref is a multiple of
+// 8, node 0 is the root and nodes 1..7 are unused); ref < 0: a leaf,
 // ~ref = level << 27 | leaf index (levels up to 15).  kr: the leaf's extinction coefficient.
 // nb[2a + (positive side)]: for a leaf, the node across that face along
 // axis a of the same level, or the leaf of a larger size that covers it

@@ -267,7 +267,11 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
         const float tmin = fminf(fminf(tn0, tn1), tn2);
         const int axis = (tn0 == tmin) ? 0 : ((tn1 == tmin) ? 1 : 2);
         const int ss = axis == 0 ? s0 : (axis == 1 ? s1 : s2);
-        const int nb = __ldg(&nodes[onode].nb[2 * axis + (ss > 0)]);
+        // a face inside the parent leads to the sibling, whose index follows
+        // from the leaf's own (children blocks start at multiples of 8);
+        // only a face on the parent's boundary needs the stored neighbour
+        const bool inner = olev > 0 && ((onode >> axis) & 1) == (ss < 0 ? 1 : 0);
+        const int nb = inner ? onode ^ (1 << axis) : __ldg(&nodes[onode].nb[2 * axis + (ss > 0)]);
         const bool out = nb < 0;
         const int2 nbh = out ? make_int2(0, 0) : __ldg(reinterpret_cast<const int2*>(nodes + nb));
         const float ds = fmaxf(tmin - tcur, 0.f);
