@@ -457,11 +457,11 @@ def main():
     achieved = per_launch_bytes / (k_ms / 1e3) / 1e9
     peak, peak_kind = peaks()
     # DRAM bytes (read + write) per packet of trace_mixed_kernel on the 256^3 disk (30.26 kB) and
-    # of trace_mixed_kernel<true> on the 8.25M-leaf octree (136.0 kB), each from one ncu capture
+    # of trace_mixed_kernel<true> on the 8.25M-leaf octree (102.0 kB), each from one ncu capture
     # of a 3e6-packet launch (summaries under profiles/), scaled by the packets of this launch;
     # None for other workloads
     traffic = (30260.0 * packets if (args.workload == "disk" and args.grid == 256) else
-               136006.1 * packets if octree else None)
+               102040.0 * packets if octree else None)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_source": peak_kind,
             "kernel": "trace_mixed_kernel<true> (octree)" if octree else "trace_mixed_kernel",
