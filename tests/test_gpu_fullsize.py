@@ -112,14 +112,19 @@ def test_torus_256_fp64_histories_follow_the_oracle(S, oracle_lib):
     compare_records(rec, r["records"], small, 1e-7, 0.999, same_n_min=1.0)
 
 
-def test_disk_octree_8m_leaves_sampled(S, oracle_lib):
+@pytest.fixture(scope="module")
+def disk_tree():
+    return W.disk_octree()
+
+
+def test_disk_octree_8m_leaves_sampled(S, oracle_lib, disk_tree):
     """The ERIS-sized octree: the exponential dust disk refined by dust mass
     into 8.25M leaves (levels 4 to 11, at most 13 levels), 1e7 packets in the
     mixed form in one graph launch; the oracle replays the first 1000 packets
     (its own tree and finest-lattice path listing).  Then the first 300
     packets in the FP64 form follow the oracle to 1e-9."""
     from parity import REL_FP64
-    tree = W.disk_octree()
+    tree = disk_tree
     assert 8.0e6 < tree.ncell < 8.5e6 and tree.max_level == 13
     prob = W.octree_problem(tree, 10_000_000, npx=512)
     grid = S.Grid(tree)
@@ -132,6 +137,19 @@ def test_disk_octree_8m_leaves_sampled(S, oracle_lib):
     grid.close()
 
 
+def test_disk_octree_40_wavelengths_sampled(S, oracle_lib, disk_tree):
+    """The same tree at 40 wavelengths (0.1-5 micron), 1e6 packets each: the
+    wavelength-major accumulation over 8.25M leaves and its transpose into the
+    [leaf, wavelength] table (2.6 GB); the oracle replays the first 40
+    packets of every wavelength."""
+    prob = W.octree_problem(disk_tree, 1_000_000, nlambda=40, npx=128)
+    grid = S.Grid(disk_tree)
+    g = _check_full_on(S, oracle_lib, prob, grid, 40, 0.995)
+    np.testing.assert_allclose(g["ledger_per_lambda"][:, 0], prob.wl.lsrc, rtol=1e-6)
+    np.testing.assert_allclose(g["absorbed"].sum(dim=0).cpu().numpy(), g["ledger_per_lambda"][:, 1], rtol=1e-6)
+    grid.close()
+
+
 def _check_full_on(S, oracle_lib, prob, grid, nrec, min_match):
     g = S.run_problem(prob, grid, precision=S.PREC_MIXED, schedule=S.SCHED_PERSISTENT, nrec=nrec, use_graph=True)
     r = oracle_lib.trace(prob, 0, nrec, nrec=nrec)
@@ -141,7 +159,7 @@ def _check_full_on(S, oracle_lib, prob, grid, nrec, min_match):
     closure = abs(led["emitted"] - led["absorbed"] - led["escaped"] - led["residual"]) / led["emitted"]
     assert closure < 1e-6
     assert float(g["absorbed"].sum()) == pytest.approx(led["absorbed"], rel=1e-6)
-    c = r["counters"] / nrec
+    c = r["counters"] / int(np.minimum(prob.npk, nrec).sum())
     assert led["scatterings"] / prob.total_packets == pytest.approx(c[0], rel=0.1)
     return g
 
