@@ -2,6 +2,7 @@
 published Philox known answers, exact geometry, the Henyey-Greenstein CDF,
 and the invariants of the direction rotation."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -9,21 +10,26 @@ import pytest
 from paper_1705_04702_gb300 import workloads as W
 
 
-# Known-answer vectors of Philox4x32 with 10 rounds, as published with the
-# generator (Salmon, Moraes, Dror & Shaw, SC'11, Random123 known-answer tests):
-# (counter, key) -> output.
-PHILOX_KAT = [
-    ((0x00000000, 0x00000000, 0x00000000, 0x00000000), (0x00000000, 0x00000000),
-     (0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8)),
-    ((0xffffffff, 0xffffffff, 0xffffffff, 0xffffffff), (0xffffffff, 0xffffffff),
-     (0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd)),
-    ((0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344), (0xa4093822, 0x299f31d0),
-     (0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1)),
-]
+def _philox_kat():
+    """Known-answer vectors of Philox4x32-10 from tests/golden (cited there):
+    (counter, key) -> output."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.txt")
+    out = []
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        ctr, key, res = (tuple(int(w, 16) for w in part.split()) for part in line.split("|"))
+        out.append((ctr, key, res))
+    return out
+
+
+PHILOX_KAT = _philox_kat()
 
 
 @pytest.mark.parametrize("ctr,key,expect", PHILOX_KAT)
 def test_philox_known_answers(oracle_lib, ctr, key, expect):
+    assert len(PHILOX_KAT) == 3
     assert tuple(oracle_lib.philox4x32_10(ctr, key)) == expect
 
 
