@@ -240,3 +240,42 @@ def test_octree_dust_source_stays_in_its_leaf(oracle_lib):
     x = r["records"][0, :, 5:8]
     assert np.all(x >= a[m]) and np.all(x <= b[m])
     assert np.ptp(x, axis=0).min() > 0.5 * (b[m] - a[m]).min()
+
+
+def test_refinement_follows_the_mass_criterion():
+    """The input generator's rule, as stated for the workloads: every box is
+    split down to min_level; beyond it a leaf below max_level holds at most
+    delta of the total mass, the parent of every deeper leaf held more, and
+    the leaves come in strictly increasing Morton order."""
+    bbox = (-24.0, 24.0, -24.0, 24.0, -24.0, 24.0)
+    dens = W.disk_density()
+    max_level, min_level, delta, sub = 7, 3, 2e-4, 2
+    tree = W.refine_octree(dens, bbox, max_level, min_level, delta, sub=sub)
+    lo = np.array(bbox[0::2])
+    ext = np.array(bbox[1::2]) - lo
+    off = (np.arange(sub) + 0.5) / sub
+
+    def mass(level, cell):
+        h = ext / 2 ** level
+        pts = np.array([lo + (np.asarray(cell) + np.array([a, b, c])) * h for a in off for b in off for c in off])
+        return dens(pts[:, 0], pts[:, 1], pts[:, 2]).mean() * np.prod(h)
+
+    n = 2 ** min_level
+    total = sum(mass(min_level, (i, j, k)) for i in range(n) for j in range(n) for k in range(n))
+    rng = np.random.default_rng(0)
+    lv = tree.leaves[:, 0]
+    assert lv.min() >= min_level and lv.max() <= max_level
+    for m in rng.choice(tree.ncell, size=300, replace=False):
+        level, ix, iy, iz = (int(v) for v in tree.leaves[m])
+        if level < max_level:
+            assert mass(level, (ix, iy, iz)) <= delta * total * (1 + 1e-12)
+        if level > min_level:
+            assert mass(level - 1, (ix // 2, iy // 2, iz // 2)) > delta * total * (1 - 1e-12)
+    corner = tree.leaves[:, 1:].astype(np.int64) << (max_level - lv[:, None].astype(np.int64))
+    key = np.zeros(tree.ncell, dtype=np.int64)
+    for bit in range(max_level):
+        for a in range(3):
+            key |= ((corner[:, a] >> bit) & 1) << (3 * bit + a)
+    assert np.all(np.diff(key) > 0)
+    c = tree.centres()
+    np.testing.assert_array_equal(tree.kr, dens(c[:, 0], c[:, 1], c[:, 2]).astype(np.float32))
