@@ -384,6 +384,15 @@ int skirt_dust_emission_pair(const double* absorbed_a, long long ncell, int n_a,
 int skirt_dust_emission_exact_static(const double* absorbed, long long ncell, int n_in, const double* lambda_in,
                                      const float* mass, double* emission, float* temperature, void* stream);
 
+/* The device random-number generator: Philox4x32-10 (Salmon, Moraes, Dror &
+ * Shaw, SC'11), the function every trace kernel draws its Monte Carlo samples
+ * with (Sect. 3.2; counter = (packet, wavelength, event, phase << 24 | block),
+ * key = (seed low, seed high)).  ctr: host uint32[n][4]; key: host
+ * uint32[n][2]; out: host uint32[n][4] receives the n output blocks.
+ * 0 <= n <= 2^24; synchronous (legacy default stream).  Errors: INVALID_ARG,
+ * NO_DEVICE, OOM, CUDA. */
+int skirt_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n);
+
 /* Microbenchmarks for the rooflines of the trace kernel (no counterpart in
  * the paper, which ran on CPUs): kind 0 FP64 FMA rate, 1 FP32 FMA rate,
  * 2 FP32<->FP64 conversion rate, 3 random-address red.global.add.f64 into a

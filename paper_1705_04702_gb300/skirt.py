@@ -85,6 +85,8 @@ def _load():
                                  ctypes.POINTER(skirt_trace_opts), ctypes.c_double, vp, vp, vp, vp]
     L.skirt_autotune.restype = i
     L.skirt_microbench.argtypes = [i, ctypes.c_longlong, _dp, ctypes.POINTER(ctypes.c_float)]
+    L.skirt_philox4x32_10.argtypes = [vp, vp, vp, i]
+    L.skirt_philox4x32_10.restype = i
     L.skirt_microbench.restype = i
     return L
 
@@ -177,6 +179,18 @@ def skirt_autotune(grid, src, wl, npackets, seed, instruments, opts, sample_frac
                               _ptr(absorbed), _ptr(images), _ptr(sed), st)
     _check(code, "skirt_autotune", (ERR_EVENT_CAP,))
     return opts
+
+
+def skirt_philox4x32_10(ctr, key):
+    """ctr: uint32 [n, 4], key: uint32 [n, 2] -> the device generator's
+    output blocks, uint32 [n, 4]."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
+    if c.shape[0] != k.shape[0]:
+        raise ValueError("ctr and key must have the same number of rows")
+    out = np.zeros_like(c)
+    _check(lib.skirt_philox4x32_10(_ptr(c), _ptr(k), _ptr(out), int(c.shape[0])), "skirt_philox4x32_10")
+    return out
 
 
 def skirt_microbench(kind, size=0):

@@ -122,3 +122,17 @@ def test_octree_leaves_are_validated_on_the_host(skirt):
     if not torch.cuda.is_available():
         code, _ = create(tree.leaves)
         assert code == skirt.ERR_NO_DEVICE
+
+
+def test_philox_entry_validates_on_the_host(skirt):
+    lib = skirt.lib
+    assert lib.skirt_philox4x32_10(None, None, None, 0) == skirt.OK
+    assert lib.skirt_philox4x32_10(None, None, None, -1) == skirt.ERR_INVALID_ARG
+    assert lib.skirt_philox4x32_10(None, None, None, 4) == skirt.ERR_INVALID_ARG
+    import torch
+    if not torch.cuda.is_available():
+        c = np.zeros((1, 4), dtype=np.uint32)
+        k = np.zeros((1, 2), dtype=np.uint32)
+        o = np.zeros((1, 4), dtype=np.uint32)
+        assert lib.skirt_philox4x32_10(c.ctypes.data_as(ctypes.c_void_p), k.ctypes.data_as(ctypes.c_void_p),
+                                       o.ctypes.data_as(ctypes.c_void_p), 1) == skirt.ERR_NO_DEVICE
