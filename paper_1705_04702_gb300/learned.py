@@ -1,7 +1,7 @@
 """The learned form of the panchromatic run: stellar emission phase, dust
 emission from the absorbed field through the MLP surrogate (exact FP64
-solver as fallback and as judge), and the dust re-emission trace
-(arXiv:1705.04702 Sect. 3.2, stellar emission phase -> dust emission phase).
+solver as fallback and as the reference the surrogate is scored against), and
+the dust re-emission trace (arXiv:1705.04702 Sect. 3.2, stellar emission phase -> dust emission phase).
 
 Every step runs in the library's kernels through the C ABI; this module only
 allocates device memory, picks the training cells and times the stages.
