@@ -168,7 +168,8 @@ typedef struct {
                           packet, books the rest as residual and returns SKIRT_ERR_EVENT_CAP */
     int peel;          /* 1: peel-off towards the instruments; 0: none (dust self-absorption) */
     int accumulate;    /* 0: outputs are zeroed first; 1: tallies are added to their contents */
-    int block;         /* threads per block (multiple of 32, <= 1024); 0 = default 256 */
+    int block;         /* threads per block: a multiple of 32, up to 256 (mixed form) or 512
+                          (FP64 form); 0 = default 256 */
     int chunk;         /* packets a thread takes per queue refill (persistent); 0 = default */
     int blocks_per_sm; /* persistent grid = blocks_per_sm x SM count; 0 = from occupancy */
     int use_graph;     /* 1: record the launch sequence in a CUDA graph, cached on the grid
@@ -190,7 +191,8 @@ typedef struct {
     double emitted, absorbed, escaped, residual; /* emitted = absorbed+escaped+residual */
     double scatterings;                           /* forced interactions */
     double deposit_steps, locate_steps, peel_steps; /* cell crossings per traversal kind */
-    int status_bits;                              /* 1 event cap, 2 source, 4 non-finite */
+    int status_bits;                              /* 1 event cap, 2 source, 4 non-finite,
+                                                     8 an octree path over its crossing bound */
     float kernel_ms;                              /* device time of the trace launches */
 } skirt_ledger;
 
@@ -214,7 +216,8 @@ typedef struct {
  * accumulate); without room for the copy they deposit in place.
  * Limits: npackets[j] < 2^32; 0 <= ninstr <= 16.
  * Errors: INVALID_ARG, OOM, CUDA; EVENT_CAP / NONFINITE / SOURCE after a
- * completed trace whose ledger flagged the condition. */
+ * completed trace whose ledger flagged the condition (NONFINITE also for an
+ * octree traversal abandoned after 3 * 2^levels + 8 crossings). */
 int skirt_trace(skirt_grid_t grid, const skirt_source* src, const skirt_wavelengths* wl,
                 const uint64_t* npackets, uint64_t seed, const skirt_instrument* ins, int ninstr,
                 const skirt_trace_opts* opts, double* absorbed, double* images, double* sed,

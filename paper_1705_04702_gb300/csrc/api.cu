@@ -662,6 +662,8 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
         ledger->kernel_ms = ms;
     }
     if (errbits & ERRBIT_NONFINITE) return fail(SKIRT_ERR_NONFINITE, "non-finite value in a packet's bookkeeping");
+    if (errbits & ERRBIT_PATH)
+        return fail(SKIRT_ERR_NONFINITE, "an octree traversal exceeded its crossing bound and was abandoned");
     if (errbits & ERRBIT_SOURCE) return fail(SKIRT_ERR_SOURCE, "a source position could not be placed in the grid");
     if (errbits & ERRBIT_EVENT_CAP) return fail(SKIRT_ERR_EVENT_CAP, "a packet reached max_events");
     g_err.clear();
