@@ -274,3 +274,51 @@ def test_zero_packets_is_a_no_op(oracle_lib):
     prob = W.sphere_problem(0)
     r = oracle_lib.trace(prob)
     assert r["status"] == 0 and np.all(r["absorbed"] == 0) and np.all(r["ledger"] == 0)
+
+
+def test_disk_source_follows_its_distributions(oracle_lib):
+    """Launch positions of the exponential-disk source (read from packets on
+    a transparent grid, which end where they start): radius ~ Gamma(2, h_R),
+    height ~ Laplace(0, h_z), azimuth uniform (Kolmogorov-Smirnov against the
+    closed-form distribution functions)."""
+    from scipy import stats
+    grid = W.uniform_grid(4, half=1000.0, kr=0.0)
+    hR, hz = 4.0, 0.4
+    prob = W.Problem("disk-launch", grid, W.Source(W.SRC_DISK, (0.0, 0.0, 0.0), h_R=hR, h_z=hz),
+                     W.single_wavelength(), np.array([20000], dtype=np.uint64))
+    r = oracle_lib.trace(prob, nrec=20000)
+    assert r["status"] == 0
+    x, y, z = r["records"][0, :, 5], r["records"][0, :, 6], r["records"][0, :, 7]
+    R = np.hypot(x, y)
+    assert stats.kstest(R, lambda v: 1 - np.exp(-v / hR) * (1 + v / hR)).pvalue > 1e-3
+    assert stats.kstest(z, stats.laplace(scale=hz).cdf).pvalue > 1e-3
+    phi = np.mod(np.arctan2(y, x), 2 * np.pi) / (2 * np.pi)
+    assert stats.kstest(phi, "uniform").pvalue > 1e-3
+    assert np.mean(R) == pytest.approx(2 * hR, rel=0.03)
+
+
+def test_dust_source_cell_frequencies(oracle_lib):
+    """The dust-cell source draws cell m with probability emission[m] / sum
+    (chi-square over 8 cells of weights 1..8, one dark cell) and a uniform
+    point inside it (per-axis fractional positions, Kolmogorov-Smirnov)."""
+    from scipy import stats
+    from oracle.selfabsorb import cell_cdf
+    grid = W.uniform_grid(2, half=1.0, kr=0.0)
+    w = np.arange(1.0, 9.0)
+    w[5] = 0.0
+    cdf, _ = cell_cdf(w[:, None])
+    n = 40000
+    prob = W.Problem("dust-launch", grid, W.Source(W.SRC_DUST), W.single_wavelength(),
+                     np.array([n], dtype=np.uint64))
+    r = oracle_lib.trace(prob, nrec=n, cell_cdf=cdf)
+    pos = r["records"][0, :, 5:8]
+    idx = np.floor(pos + 1.0).astype(int)  # cell size 1 over [-1, 1]
+    m = (idx[:, 2] * 2 + idx[:, 1]) * 2 + idx[:, 0]
+    counts = np.bincount(m, minlength=8)
+    assert counts[5] == 0
+    keep = w > 0
+    expect = n * w[keep] / w.sum()
+    assert stats.chisquare(counts[keep], expect).pvalue > 1e-3
+    frac = pos + 1.0 - idx
+    for a in range(3):
+        assert stats.kstest(frac[:, a], "uniform").pvalue > 1e-3
