@@ -322,3 +322,27 @@ def test_dust_source_cell_frequencies(oracle_lib):
     frac = pos + 1.0 - idx
     for a in range(3):
         assert stats.kstest(frac[:, a], "uniform").pvalue > 1e-3
+
+
+def test_slab_beam_per_wavelength_extinction_and_luminosity(oracle_lib):
+    """Three wavelengths through one pure-absorber slab: wavelength j sees
+    optical depth kscale_j tau, launches lsrc_j / npackets_j per packet, so its
+    transmitted and per-layer absorbed luminosities are lsrc_j e^{-kscale_j tau}
+    and lsrc_j (e^{-kscale_j tau_{l-1}} - e^{-kscale_j tau_l}), exact to rounding."""
+    layer_tau = np.array([0.3, 0.9, 0.4], dtype=np.float32).astype(np.float64)
+    grid = W.slab_grid(layer_tau)
+    kscale = np.array([0.5, 1.0, 2.5])
+    lsrc = np.array([1.0, 2.0, 3.0])
+    npk = np.array([1, 2, 3], dtype=np.uint64)
+    wl = W.Wavelengths(lam=np.array([1.0, 0.55, 0.3]), kscale=kscale, albedo=np.zeros(3), g=np.zeros(3), lsrc=lsrc)
+    prob = W.Problem("slab-3", grid, W.Source(W.SRC_BEAM, (0.1, 0.2, 0.0), (0.0, 0.0, 1.0)), wl, npk)
+    r = oracle_lib.trace(prob, nrec=3)
+    assert r["status"] == 0
+    cum = np.concatenate([[0.0], np.cumsum(layer_tau)])
+    for j in range(3):
+        esc = r["ledger"][j, 2]
+        assert esc == pytest.approx(lsrc[j] * math.exp(-kscale[j] * cum[-1]), rel=1e-14)
+        got = r["absorbed"][:, j].reshape(grid.nz, -1).sum(axis=1)
+        expect = lsrc[j] * (np.exp(-kscale[j] * cum[:-1]) - np.exp(-kscale[j] * cum[1:]))
+        np.testing.assert_allclose(got, expect, rtol=1e-13)
+        assert r["ledger"][j, 0] == pytest.approx(lsrc[j], rel=1e-15)
