@@ -144,3 +144,39 @@ def test_bf16_rounding():
     assert r[2] == 1 + 2 ** -7              # above halfway: rounds up
     assert r[3] == -2.5 and r[4] == 3.140625
     assert abs(r[5] - 1e-20) / 1e-20 < 2 ** -8
+
+
+def test_mlp_forward_on_a_scalar_chain():
+    """The network's wiring on weights with one path: input feature 7
+    (standardised with its own mean and std) -> hidden unit 5 -> hidden unit
+    11 -> output bin 42, every other weight and bias zero except b3[3].  The
+    output is then a two-level softmax written out by hand: bin 42 takes
+    e^{z}, bin 3 e^{b}, the other 98 bins 1 each, with
+    z = g * s(b2 + w2 * s(w1 * x7)), s(v) = v / (1 + e^{-v})."""
+    import math
+    P = {"W1": np.zeros((128, 32)), "b1": np.zeros(128), "W2": np.zeros((128, 128)), "b2": np.zeros(128),
+         "W3": np.zeros((100, 128)), "b3": np.zeros(100)}
+    w1, w2, b2, g, b = 0.8, -1.3, 0.25, 2.0, -0.7
+    P["W1"][5, 7] = w1
+    P["W2"][11, 5] = w2
+    P["b2"][11] = b2
+    P["W3"][42, 11] = g
+    P["b3"][3] = b
+    x = np.zeros((3, 32))
+    x[:, 7] = [0.5, -2.0, 3.0]
+    x[:, 6] = 9.0  # a neighbouring feature with no path to the output
+    mean, std = np.zeros(32), np.ones(32)
+    mean[7], std[7] = 0.2, 2.0
+    tot = np.array([1.0, 10.0, 0.5])
+    em = E.surrogate_emission(P, x, tot, mean, std)
+
+    def s(v):
+        return v / (1.0 + math.exp(-v))
+    for r in range(3):
+        x7 = (x[r, 7] - 0.2) / 2.0
+        z = g * s(b2 + w2 * s(w1 * x7))
+        den = math.exp(z) + math.exp(b) + 98.0
+        assert em[r, 42] == pytest.approx(tot[r] * math.exp(z) / den, rel=1e-13)
+        assert em[r, 3] == pytest.approx(tot[r] * math.exp(b) / den, rel=1e-13)
+        others = np.delete(em[r], [3, 42])
+        np.testing.assert_allclose(others, tot[r] / den, rtol=1e-13)
