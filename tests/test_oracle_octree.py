@@ -279,3 +279,20 @@ def test_refinement_follows_the_mass_criterion():
     assert np.all(np.diff(key) > 0)
     c = tree.centres()
     np.testing.assert_array_equal(tree.kr, dens(c[:, 0], c[:, 1], c[:, 2]).astype(np.float32))
+
+
+def test_octree_descriptions_refuse_bad_inputs():
+    """Host-side checks of the octree description helpers: a uniform tree
+    needs a 2^L cube, and a finest-level leaf cannot be split."""
+    with pytest.raises(ValueError):
+        W.octree_from_grid(W.uniform_grid(6))
+    with pytest.raises(ValueError):
+        W.octree_from_grid(W.Grid(4, 4, 8, (-1, 1, -1, 1, -1, 1), np.zeros((8, 4, 4), np.float32)))
+    tree = W.octree_from_grid(W.uniform_grid(4))
+    with pytest.raises(ValueError):
+        W.split_leaves(tree, [0])
+    deeper = dataclasses.replace(tree, max_level=3)
+    split = W.split_leaves(deeper, [0, 5])
+    assert split.ncell == tree.ncell + 14
+    a, b = split.boxes()
+    np.testing.assert_allclose(np.prod(b - a, axis=1).sum(), 8.0, rtol=1e-14)
