@@ -9,10 +9,16 @@ tallies) by one persistent launch replayed from a CUDA graph.  Inputs are
 resident in HBM when the timed region starts; L2 is flushed (256 MB write)
 before every timed step.
 
-Reported next to it: the plain FP64 form on 1e7 packets of the same
-workload, the end-to-end time through the C ABI with pinned host buffers,
-the rooflines of the trace kernel (HBM bytes and FP64 reductions), and the
-CPU FP64 oracle timed on a sample, on one core and on every host core.
+The schedule (block size, refill chunk, resident blocks, step_min) is picked
+by the library's autotuner on a 2% sample before the timed region; the
+default schedule is timed beside it.  Reported next to the headline: the
+plain FP64 form on 1e7 packets of the same workload, the end-to-end time
+through the C ABI with pinned host buffers, the rooflines of the trace
+kernel (HBM bytes, FP64 reductions, the binding one as "roofline"), the CPU
+FP64 oracle timed on a sample, on one core and on every host core, and the
+batched form ("batched": the clumpy torus with 200 wavelengths of uneven
+packet counts, 7.5e8 packets, one persistent graph launch) with its own
+rooflines and the plain FP64 form through the same persistent schedule.
 
 `--impl reference` times the oracle (the slow, plain CPU program the
 parity tests compare against) on every host core instead.
@@ -49,14 +55,23 @@ def parse():
                          "every finest-lattice plane)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="trace with the default schedule instead of the autotuned one")
+    ap.add_argument("--tune-fraction", type=float, default=0.02, help="autotuner sample (fraction of the packets)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-form (200-wavelength torus) record")
+    ap.add_argument("--batched-steps", type=int, default=1)
+    ap.add_argument("--batched-fp64-fraction", type=float, default=0.005,
+                    help="plain FP64 sample of the batched form (fraction of its packets)")
     ap.add_argument("--epochs", type=int, default=60, help="learned workload: training epochs")
     ap.add_argument("--lr", type=float, default=2e-3, help="learned workload: Adam step size")
-    ap.add_argument("--workload", default="disk", choices=["disk", "disk40", "torus", "octree", "learned", "selfabs"],
+    ap.add_argument("--cells", type=int, default=2_000_000, help="exact workload: cells")
+    ap.add_argument("--workload", default="disk",
+                    choices=["disk", "disk40", "torus", "octree", "learned", "selfabs", "exact"],
                     help="disk: 1 wavelength, --packets packets (default); disk40: 40 wavelengths, "
                          "--packets per wavelength; torus: clumpy torus, 200 wavelengths, uneven counts "
                          "(--packets scales them, 1e8 = the full 7.5e8-packet run); octree: the disk galaxy "
-                         "on an 8.25M-leaf octree, 1 wavelength, --packets packets")
+                         "on an 8.25M-leaf octree, 1 wavelength, --packets packets; exact: the exact dust "
+                         "emission solve of --cells synthetic cells with 200 absorbed wavelengths")
     a = ap.parse_args()
     if a.cpu_packets is None:
         a.cpu_packets = 2000 if a.workload == "octree" else 60000
@@ -295,6 +310,33 @@ def run_learned_report(args):
                       **rep}), flush=True)
 
 
+def run_exact_report(args):
+    """The exact FP64 dust-emission solve (equilibrium temperatures of three
+    grain populations, 100 emission wavelengths) on --cells synthetic cells
+    absorbing on 200 wavelengths 0.09-10 um: device time per call, as one
+    JSON line (not the headline metric)."""
+    import torch
+    from paper_1705_04702_gb300 import build
+    from paper_1705_04702_gb300 import workloads as W
+    build.build()
+    from paper_1705_04702_gb300 import skirt as S
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    lam = np.geomspace(0.09, 10.0, 200)
+    a, m = W.absorbed_spectra(args.cells, lam, seed=3)
+    a_d = torch.as_tensor(a, dtype=torch.float64, device="cuda")
+    m_d = torch.as_tensor(m, dtype=torch.float32, device="cuda")
+    del a
+    em = torch.empty((args.cells, S.NEMIT), dtype=torch.float64, device="cuda")
+    ms = []
+    for _ in range(args.warmup + args.steps):
+        st = S.skirt_dust_emission(a_d, args.cells, lam.size, lam, m_d, S.EMIT_EXACT, None, em)
+        ms.append(st["ms_exact"])
+    ms = ms[args.warmup:]
+    print(json.dumps({"report": "exact dust emission", "cells": args.cells, "n_in": int(lam.size),
+                      "ms_per_call": float(np.mean(ms)), "cells_per_s": args.cells / (np.mean(ms) / 1e3)}),
+          flush=True)
+
+
 def run_selfabs_report(args):
     """Dust self-absorption cycles on the clumpy torus (256^3, 200 stellar
     wavelengths, then 1e6 dust packets per emission wavelength per cycle):
@@ -341,6 +383,103 @@ def run_selfabs_report(args):
 
 
 # ----------------------------------------------------------------------- ours
+# Warp instructions per packet of trace_mixed_kernel on the 256^3 disk, from
+# the committed ncu capture of the kernel as it stands
+# (profiles/trace_mixed_kernel_disk256_3e6_full.md); None when the kernel has
+# changed since.
+ISSUE_INST_PER_PACKET = None
+# DRAM bytes (read + write) per packet of the trace kernel from one ncu
+# capture of a 3e6-packet launch of the kernel as it stands (profiles/),
+# scaled by the packets of the launch; None when the kernel has changed since.
+TRAFFIC_PER_PACKET = {"disk": None, "octree": None}
+
+
+def trace_rooflines(led, packets, k_ms, ninstr, red_rate, peak, peak_kind, kernel, crossing_bytes, traffic_pp,
+                    clock_mhz=None, sm_count=None):
+    """Rooflines of one trace launch: algorithmic bytes
+    (the crossing's read, a 16-byte read-modify-write per deposit and per
+    peel-off tally) against the measured copy bandwidth; FP64 reductions (one
+    per deposit and per tally) against the random red.f64 rate measured in the
+    same run; the bound is the one that binds (the larger fraction)."""
+    steps = led["deposit_steps"] + led["locate_steps"] + led["peel_steps"]
+    tallies = (packets + led["scatterings"]) * ninstr
+    byts = crossing_bytes * steps + 16 * led["deposit_steps"] + 16 * tallies
+    t = k_ms / 1e3
+    hbm = {"bound": "hbm", "achieved": byts / t / 1e9, "peak": peak, "unit": "GB/s",
+           "frac": byts / t / 1e9 / peak, "traffic": traffic_pp * packets if traffic_pp else None,
+           "peak_source": peak_kind, "kernel": kernel, "kernel_ms": k_ms, "algorithmic_bytes_per_launch": byts,
+           "per_packet": {"deposit_steps": led["deposit_steps"] / packets, "locate_steps": led["locate_steps"] / packets,
+                          "peel_steps": led["peel_steps"] / packets, "scatterings": led["scatterings"] / packets}}
+    reds = led["deposit_steps"] + tallies
+    atom = {"bound": "atomics", "achieved": reds / t, "peak": red_rate, "unit": "red.f64/s",
+            "frac": reds / t / red_rate, "traffic": hbm["traffic"], "kernel": kernel, "kernel_ms": k_ms,
+            "atomics_per_packet": reds / packets,
+            "peak_source": "measured in this run: random red.global.add.f64 into a table of the absorbed table's size"}
+    binding = dict(atom if atom["frac"] >= hbm["frac"] else hbm)
+    binding["min_of"] = {"hbm_frac": hbm["frac"], "atomics_frac": atom["frac"]}
+    out = {"roofline": binding, "roofline_hbm": hbm, "roofline_atomic": atom}
+    if ISSUE_INST_PER_PACKET and clock_mhz and sm_count:
+        cap = sm_count * 4 * clock_mhz * 1e6 / ISSUE_INST_PER_PACKET
+        out["roofline_issue"] = {"bound": "issue", "achieved": packets / t, "peak": cap, "unit": "packets/s",
+                                 "frac": packets / t / cap, "warp_inst_per_packet": ISSUE_INST_PER_PACKET,
+                                 "note": "4 warp instructions per SM per cycle at the median SM clock of the run"}
+    return out
+
+
+def run_steps(S, grid, src, tables, prob, seed, ins, opts, outs, steps, warmup, flush, stream, barrier, clocks=None):
+    """warmup untimed then `steps` timed trace calls (L2 flushed before
+    each; the clock sampler, if given, runs over the timed calls); returns
+    (elapsed seconds, per-launch kernel ms, last ledger)."""
+    import torch
+    absorbed, images, sed = outs
+
+    def step():
+        return S.skirt_trace(grid.h, src, tables.c, prob.npk, seed, ins, opts, absorbed, images, sed,
+                             stream=stream.cuda_stream)
+
+    for _ in range(warmup):
+        flush.zero_()
+        step()
+    barrier()
+    if clocks is not None:
+        clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    kernel_ms = []
+    led = None
+    ev0.record(stream)
+    for _ in range(steps):
+        flush.zero_()
+        _, led, _ = step()
+        kernel_ms.append(led["kernel_ms"])
+    ev1.record(stream)
+    barrier()
+    return ev0.elapsed_time(ev1) / 1e3, kernel_ms, led
+
+
+def plain_fp64(S, grid, src, tables, prob, seed, ins, outs, fraction, schedule, stream, barrier):
+    """The plain FP64 form on a sample of the workload (every wavelength's
+    packets scaled by fraction): one warm-up call, then one timed call."""
+    absorbed, images, sed = outs
+    p64 = prob.with_packets(np.maximum(np.round(prob.npk.astype(np.float64) * fraction), prob.npk > 0)
+                            .astype(np.uint64))
+    o64 = S.skirt_trace_opts_default()
+    o64.precision = S.PREC_FP64
+    o64.schedule = schedule
+    small = prob.with_packets(np.minimum(p64.npk, 1000))
+    S.skirt_trace(grid.h, src, tables.c, small.npk, seed, ins, o64, absorbed, images, sed, stream=stream.cuda_stream)
+    barrier()
+    t0 = time.perf_counter()
+    _, l64, _ = S.skirt_trace(grid.h, src, tables.c, p64.npk, seed, ins, o64, absorbed, images, sed,
+                              stream=stream.cuda_stream)
+    barrier()
+    dt = time.perf_counter() - t0
+    return {"value": p64.total_packets / dt, "unit": UNIT, "packets": p64.total_packets, "kernel_ms": l64["kernel_ms"],
+            "precision": "fp64",
+            "schedule": "persistent (one launch for all wavelengths)" if schedule == S.SCHED_PERSISTENT
+            else "one launch per wavelength"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -351,6 +490,9 @@ def main():
         return
     if args.workload == "selfabs":
         run_selfabs_report(args)
+        return
+    if args.workload == "exact":
+        run_exact_report(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -402,6 +544,7 @@ def main():
     absorbed = torch.zeros((grid.ncell, n), dtype=torch.float64, device="cuda")
     images = torch.zeros(npix, dtype=torch.float64, device="cuda")
     sed = torch.zeros((len(prob.instruments), n), dtype=torch.float64, device="cuda")
+    outs = (absorbed, images, sed)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     tables = S.Tables(prob.wl)
@@ -411,65 +554,47 @@ def main():
     opts.precision = S.PREC_MIXED
     opts.schedule = S.SCHED_PERSISTENT
     opts.use_graph = 1
-    tune = None
-    if args.autotune:
-        S.skirt_autotune(grid.h, src, tables.c, prob.npk, seed, ins, opts, 0.02, absorbed, images, sed,
-                         stream=stream.cuda_stream)
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    tune = {"block": opts.block, "chunk": opts.chunk, "blocks_per_sm": opts.blocks_per_sm,
+            "step_min": opts.step_min, "autotuned": False}
+    default_opts = None
+    if not args.no_autotune:
+        default_opts = S.skirt_trace_opts()
+        ctypes_copy(default_opts, opts)
+        rep = S.skirt_autotune(grid.h, src, tables.c, prob.npk, seed, ins, opts, args.tune_fraction, absorbed,
+                               images, sed, stream=stream.cuda_stream, repeats=2)
+        ch = rep["points"][rep["chosen"]]
         tune = {"block": opts.block, "chunk": opts.chunk, "blocks_per_sm": opts.blocks_per_sm,
-                "step_min": opts.step_min, "autotuned": True}
+                "step_min": opts.step_min, "autotuned": True, "candidates": rep["n"],
+                "sample_packets": rep["sample_packets"], "repeats": rep["repeats"],
+                "sample_ms_chosen": ch["ms"], "sample_ms_default": rep["points"][0]["ms"],
+                "chosen_is_default": rep["chosen"] == 0}
 
-    def step():
-        return S.skirt_trace(grid.h, src, tables.c, prob.npk, seed, ins, opts, absorbed, images, sed,
-                             stream=stream.cuda_stream)
-
-    for _ in range(args.warmup):
-        flush.zero_()
-        step()
-    barrier()
     clocks = ClockSampler(local)
-    clocks.start()
-    kernel_ms = []
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    barrier()
-    ev0.record(stream)
-    led = None
-    for _ in range(args.steps):
-        flush.zero_()
-        _, led, _ = step()
-        kernel_ms.append(led["kernel_ms"])
-    ev1.record(stream)
-    barrier()
+    elapsed, kernel_ms, led = run_steps(S, grid, src, tables, prob, seed, ins, opts, outs, args.steps, args.warmup,
+                                        flush, stream, barrier, clocks)
     clk = clocks.stop()
-    elapsed = job_time(ev0.elapsed_time(ev1) / 1e3, dist, "cuda")
+    elapsed = job_time(elapsed, dist, "cuda")
     packets = prob.total_packets
     value = job_throughput(packets, world, args.steps, elapsed)
+    if default_opts is not None:
+        # the default schedule on the same workload, for comparison with the tuned one
+        k = min(args.steps, 3)
+        e_def, _, _ = run_steps(S, grid, src, tables, prob, seed, ins, default_opts, outs, k, 1, flush, stream,
+                                barrier)
+        tune["default_value"] = job_throughput(packets, world, k, job_time(e_def, dist, "cuda"))
+        tune["default_steps"] = k
 
-    # ---- roofline of the trace kernel: algorithmic bytes per launch (per
-    # crossing the cell's kr; on the octree the next leaf's node head, 8 B,
-    # and the face-neighbour index, 4 B)
+    # ---- rooflines of the trace kernel
     octree = args.workload == "octree"
-    kr_b = 12 if octree else 4
-    per_launch_bytes = (kr_b * (led["deposit_steps"] + led["locate_steps"] + led["peel_steps"])
-                        + 16 * led["deposit_steps"]
-                        + 16 * (packets + led["scatterings"]) * len(prob.instruments))
-    k_ms = float(np.mean(kernel_ms))
-    achieved = per_launch_bytes / (k_ms / 1e3) / 1e9
     peak, peak_kind = peaks()
-    # DRAM bytes (read + write) per packet of trace_mixed_kernel on the 256^3 disk (30.26 kB) and
-    # of trace_mixed_kernel<true> on the 8.25M-leaf octree (102.0 kB), each from one ncu capture
-    # of a 3e6-packet launch (summaries under profiles/), scaled by the packets of this launch;
-    # None for other workloads
-    traffic = (30260.0 * packets if (args.workload == "disk" and args.grid == 256) else
-               102040.0 * packets if octree else None)
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "peak_source": peak_kind,
-            "kernel": "trace_mixed_kernel<true> (octree)" if octree else "trace_mixed_kernel",
-            "kernel_ms": k_ms, "algorithmic_bytes_per_launch": per_launch_bytes,
-            "per_packet": {"deposit_steps": led["deposit_steps"] / packets,
-                           "locate_steps": led["locate_steps"] / packets,
-                           "peel_steps": led["peel_steps"] / packets,
-                           "scatterings": led["scatterings"] / packets}}
+    red_rate, _ = S.skirt_microbench(3, grid.ncell * n)
+    k_ms = float(np.mean(kernel_ms))
+    key = "octree" if octree else ("disk" if args.workload == "disk" and args.grid == 256 else None)
+    roofs = trace_rooflines(led, packets, k_ms, len(prob.instruments), red_rate, peak, peak_kind,
+                            "trace_mixed_kernel<true> (octree)" if octree else "trace_mixed_kernel",
+                            12 if octree else 4, TRAFFIC_PER_PACKET.get(key) if key else None,
+                            clk["sm_mhz"] if clk else None, sm_count if key == "disk" else None)
 
     # ---- the same at 32-byte sector granularity (context): one sector per
     # crossing's read, and a read plus a write-back sector per FP64 reduction
@@ -481,34 +606,12 @@ def main():
                    "note": "context: 32-byte sector per crossing read, read + write-back sector per reduction; "
                            "L2 reuse lets this exceed the DRAM bytes actually moved"}
 
-    # ---- atomic roofline: FP64 reductions per packet (one per deposit, one per
-    # peel-off tally) against the measured random red.f64 rate into a table
-    # the size of this absorbed table
-    red_rate, _ = S.skirt_microbench(3, grid.ncell * n)
-    atomics_pp = (led["deposit_steps"] + (packets + led["scatterings"]) * len(prob.instruments)) / packets
-    roof_atomic = {"bound": "atomics", "achieved": value / world * atomics_pp, "peak": red_rate,
-                   "unit": "red.f64/s", "frac": value / world * atomics_pp / red_rate,
-                   "atomics_per_packet": atomics_pp,
-                   "peak_source": f"measured in this run: random red.global.add.f64 into {grid.ncell * n} doubles"}
-
-    # ---- plain FP64 form, one launch per wavelength, on a sample
+    # ---- plain FP64 form on a sample
     fp64 = None
     if args.fp64_packets > 0:
-        frac64 = min(1.0, args.fp64_packets / max(prob.total_packets, 1))
-        p64 = prob.with_packets(np.round(prob.npk.astype(np.float64) * frac64).astype(np.uint64))
-        o64 = S.skirt_trace_opts_default()
-        o64.precision = S.PREC_FP64
-        o64.schedule = S.SCHED_PER_LAMBDA
-        S.skirt_trace(grid.h, src, tables.c, p64.npk, seed, ins, o64, absorbed, images, sed,
-                      stream=stream.cuda_stream)
-        barrier()
-        t0 = time.perf_counter()
-        _, l64, _ = S.skirt_trace(grid.h, src, tables.c, p64.npk, seed, ins, o64, absorbed, images, sed,
-                                  stream=stream.cuda_stream)
-        barrier()
-        dt64 = time.perf_counter() - t0
-        fp64 = {"value": p64.total_packets / dt64, "unit": UNIT, "packets": p64.total_packets,
-                "kernel_ms": l64["kernel_ms"], "precision": "fp64", "schedule": "per-wavelength launch"}
+        fp64 = plain_fp64(S, grid, src, tables, prob, seed, ins, outs,
+                          min(1.0, args.fp64_packets / max(prob.total_packets, 1)),
+                          S.SCHED_PER_LAMBDA if n == 1 else S.SCHED_PERSISTENT, stream, barrier)
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
@@ -542,6 +645,14 @@ def main():
             d2h += 4 * nl
         e2e = {"value": packets * world / dte, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": ksteps}
+    grid.close()
+    del absorbed, images, sed, outs
+
+    # ---- the batched form: the clumpy torus, 200 wavelengths with uneven
+    # packet counts, in one persistent graph launch
+    batched = None
+    if args.workload == "disk" and not args.no_batched:
+        batched = run_batched(S, args, seed, opts, flush, stream, barrier, peak, peak_kind, dist, world)
 
     if rank == 0:
         line = {
@@ -549,23 +660,72 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": config_of(args, prob, {"precision": "mixed", "schedule": "persistent + CUDA graph",
-                                             "replicas": world, "tuning": tune or {
-                                                 "block": opts.block, "chunk": opts.chunk,
-                                                 "blocks_per_sm": opts.blocks_per_sm}}),
-            "roofline": roof,
-            "roofline_atomic": roof_atomic,
+                                             "replicas": world, "tuning": tune}),
+            **roofs,
             "roofline_sector": roof_sector,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": args.steps * (1 + len(prob.instruments)),
+            "gpu_launches": args.steps * (1 + len(prob.instruments) + (1 if n > 1 else 0)),
             "clocks": clk,
             "plain_fp64": fp64,
             "speedup_vs_plain_fp64": (value / world / fp64["value"]) if fp64 else None,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
-    grid.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def ctypes_copy(dst, src):
+    import ctypes
+    ctypes.memmove(ctypes.addressof(dst), ctypes.addressof(src), ctypes.sizeof(src))
+
+
+def run_batched(S, args, seed, opts, flush, stream, barrier, peak, peak_kind, dist, world):
+    """The batched form (clumpy torus 256^3, 200 wavelengths, 1e5-2e7 packets
+    each, 7.5e8 in all): one warm-up and args.batched_steps timed graph
+    launches with the tuned schedule, its rooflines, and the plain FP64 form
+    through the same persistent schedule on a sample."""
+    import torch
+    prob = W_torus(args)
+    prob.seed = seed
+    grid = S.Grid(prob.grid)
+    n = prob.wl.n
+    npix = sum(i.npx * i.npx for i in prob.instruments) * n
+    outs = (torch.zeros((grid.ncell, n), dtype=torch.float64, device="cuda"),
+            torch.zeros(npix, dtype=torch.float64, device="cuda"),
+            torch.zeros((len(prob.instruments), n), dtype=torch.float64, device="cuda"))
+    tables = S.Tables(prob.wl)
+    ins = S.make_instruments(prob.instruments)
+    src = S.make_source(prob.source)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    el, kms, led = run_steps(S, grid, src, tables, prob, seed, ins, opts, outs, args.batched_steps, 1, flush, stream,
+                             barrier, clocks)
+    clk = clocks.stop()
+    el = job_time(el, dist, "cuda")
+    packets = prob.total_packets
+    value = job_throughput(packets, world, args.batched_steps, el)
+    red_rate, _ = S.skirt_microbench(3, grid.ncell * n)
+    roofs = trace_rooflines(led, packets, float(np.mean(kms)), len(prob.instruments), red_rate, peak, peak_kind,
+                            "trace_mixed_kernel", 4, None)
+    closure = abs(led["emitted"] - led["absorbed"] - led["escaped"] - led["residual"]) / led["emitted"]
+    fp64 = plain_fp64(S, grid, src, tables, prob, seed, ins, outs, args.batched_fp64_fraction, S.SCHED_PERSISTENT,
+                      stream, barrier)
+    grid.close()
+    del outs
+    torch.cuda.empty_cache()
+    return {"workload": workload_name(argparse.Namespace(**{**vars(args), "workload": "torus", "packets": 1e8}),
+                                      prob),
+            "value": value, "unit": UNIT, "steps": args.batched_steps, "warmup": 1,
+            "ms_per_step": 1e3 * el / args.batched_steps, "packets_per_step": packets,
+            "schedule": "persistent + CUDA graph, the headline's tuned schedule", **roofs,
+            "ledger_closure": closure, "clocks": clk, "plain_fp64": fp64,
+            "speedup_vs_plain_fp64": value / world / fp64["value"]}
+
+
+def W_torus(args):
+    from paper_1705_04702_gb300 import workloads as W
+    return W.torus_problem(n=args.grid, nlambda=200, npx=512)
 
 
 if __name__ == "__main__":

@@ -181,6 +181,18 @@ typedef struct {
     int nrec;          /* >= 0: per-packet records for packet indices < nrec */
     double* records;   /* device-or-host double[n][nrec][8]: scatterings, escaped, absorbed,
                           residual, peeled flux, x, y, z of the last interaction */
+    /* Packet ranges (the task split of Sect. 5.2: each process launches its own
+     * share of every wavelength's packets and the tables are summed).  Both
+     * host uint64[n] or NULL.  Packet i (0 <= i < npackets[j]) of wavelength j
+     * is packet first_packet[j] + i of the run: that index keys its random
+     * stream, while records stay indexed by i.  The luminosity per packet is
+     * lsrc[j] / total_packets[j].  NULL first_packet means all zeros, NULL
+     * total_packets means npackets.  Then first_packet[j] + npackets[j] must
+     * not exceed total_packets[j], nor 2^32.  Calls over disjoint ranges of the
+     * same run therefore trace exactly the packets of one call over all of
+     * them, and their tables add up to its tables. */
+    const uint64_t* first_packet;
+    const uint64_t* total_packets;
 } skirt_trace_opts;
 
 /* Fills *opts with the defaults (mixed precision, persistent, peel on). */
@@ -226,16 +238,32 @@ int skirt_trace(skirt_grid_t grid, const skirt_source* src, const skirt_waveleng
 /* Autotuner (the GPU counterpart of choosing the hybrid scheme for the
  * hardware, Sect. 6.2): times the persistent schedule on a sample of
  * the workload (every npackets[j] scaled by sample_fraction, at least one
- * packet where npackets[j] > 0) over block sizes {64, 128, 256} (and 512 for
- * the FP64 form), refill chunks {1, 4, 16}, step_min {16, 20, 24} (mixed
- * form) and resident blocks per SM from the occupancy limit down, halving,
- * and writes the fastest block / chunk / blocks_per_sm / step_min into
- * *opts.  The outputs are used as scratch and left zeroed.  Errors as
- * skirt_trace. */
+ * packet where npackets[j] > 0).  Candidates: the schedule *opts asks for
+ * (its zero fields at their defaults), then block sizes {64, 128, 256} (and
+ * 512 for the FP64 form) x refill chunks {1, 4, 16} x step_min {16, 20, 24}
+ * (mixed form) x resident blocks per SM from the occupancy limit down,
+ * halving.  After one untimed warm-up launch, every candidate is timed
+ * `repeats` times (<= 0 selects 2) and scored by its fastest launch.  The
+ * fastest candidate replaces the requested schedule only if it is faster by
+ * more than 2%; the result is written into opts->block / chunk /
+ * blocks_per_sm / step_min.  report (may be NULL) receives the sweep.  The
+ * outputs are used as scratch and left zeroed.  Errors as skirt_trace. */
+enum { SKIRT_TUNE_MAX_POINTS = 256 };
+typedef struct {
+    int block, chunk, blocks_per_sm, step_min;
+    float ms;                /* fastest of the repeats, device time of the trace launch */
+} skirt_tune_point;
+typedef struct {
+    int n;                   /* candidates timed; point 0 is the requested schedule */
+    int chosen;              /* index of the schedule written into opts */
+    int repeats;
+    unsigned long long sample_packets;
+    skirt_tune_point points[SKIRT_TUNE_MAX_POINTS];
+} skirt_tune_report;
 int skirt_autotune(skirt_grid_t grid, const skirt_source* src, const skirt_wavelengths* wl,
                    const uint64_t* npackets, uint64_t seed, const skirt_instrument* ins, int ninstr,
-                   skirt_trace_opts* opts, double sample_fraction, double* absorbed,
-                   double* images, double* sed, void* stream);
+                   skirt_trace_opts* opts, double sample_fraction, int repeats, double* absorbed,
+                   double* images, double* sed, skirt_tune_report* report, void* stream);
 
 /* ---------------------------------------------------------- dust emission */
 /* Dust emission phase (Sect. 3.2: the emission spectrum of every dust cell

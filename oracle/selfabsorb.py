@@ -47,10 +47,16 @@ def cell_cdf(emission):
 
 
 def self_absorption(grid, absorbed_star, lam_star, mass, packets_per_lambda, seed, tol=1e-2, max_cycles=10,
-                    wl=None):
+                    wl=None, batches=1):
     """The cycles on a workloads.Grid; returns the absorbed dust table of the
     last cycle, the emission that fed it, the cycle count, whether the total
-    converged, and per cycle the emitted and re-absorbed dust luminosity."""
+    converged, and per cycle the emitted and re-absorbed dust luminosity.
+
+    batches > 1 traces every cycle's packets as that many disjoint packet
+    ranges (the same packets; the table is their sum) and adds the Monte
+    Carlo error estimates of the batch means method: per cycle the variance
+    of the absorbed total ("var_absorbed"), and the variance of every entry of
+    the last cycle's table ("var_absorbed_dust")."""
     lam_em, _ = emission_grid()
     wl = dust_wavelengths() if wl is None else wl
     absorbed_dust = None
@@ -66,14 +72,41 @@ def self_absorption(grid, absorbed_star, lam_star, mass, packets_per_lambda, see
         npk = np.where(totals > 0, int(packets_per_lambda), 0).astype(np.uint64)
         prob = W.Problem("dust self-absorption cycle", grid, W.Source(W.SRC_DUST),
                          dataclasses.replace(wl, lsrc=totals), npk, [], seed=seed, phase=PHASE0 + k)
-        r = trace(prob, peel=False, cell_cdf=cdf)
+        if batches <= 1:
+            r = trace(prob, peel=False, cell_cdf=cdf)
+            var_tab = None
+        else:
+            r, var_tab = _batched_trace(prob, cdf, int(packets_per_lambda), batches)
         history.append({"emitted": float(totals.sum()), "absorbed": float(r["ledger"][:, 1].sum()),
                         "ledger": r["ledger"], "status": r["status"]})
+        if var_tab is not None:
+            history[-1]["var_absorbed"] = float(r["var_total"])
         absorbed_dust = r["absorbed"]
         if k > 0:
             prev, cur = history[-2]["absorbed"], history[-1]["absorbed"]
             if abs(cur - prev) <= tol * (history[0]["emitted"] + cur):
                 converged = True
                 break
-    return {"absorbed_dust": absorbed_dust, "emission": emission, "cycles": len(history), "converged": converged,
-            "history": history}
+    out = {"absorbed_dust": absorbed_dust, "emission": emission, "cycles": len(history), "converged": converged,
+           "history": history}
+    if batches > 1:
+        out["var_absorbed_dust"] = var_tab
+    return out
+
+
+def _batched_trace(prob, cdf, npk, batches):
+    """The trace of prob as `batches` disjoint packet ranges: the summed
+    result, plus the batch-means variance estimate of every table entry and
+    of the absorbed total (variance of the sum = B/(B-1) sum_b (x_b - x/B)^2)."""
+    edges = np.linspace(0, npk, batches + 1).round().astype(np.int64)
+    parts = [trace(prob, int(a), int(b), peel=False, cell_cdf=cdf) for a, b in zip(edges[:-1], edges[1:])]
+    tab = np.sum([p["absorbed"] for p in parts], axis=0)
+    led = np.sum([p["ledger"] for p in parts], axis=0)
+    B = float(batches)
+    var_tab = B / (B - 1.0) * np.sum([(p["absorbed"] - tab / B) ** 2 for p in parts], axis=0)
+    tot = np.array([p["ledger"][:, 1].sum() for p in parts])
+    var_tot = B / (B - 1.0) * np.sum((tot - tot.sum() / B) ** 2)
+    status = 0
+    for p in parts:
+        status |= p["status"]
+    return {"absorbed": tab, "ledger": led, "status": status, "var_total": var_tot}, var_tab

@@ -65,7 +65,7 @@ constexpr double kPi = 3.14159265358979323846;
 namespace {
 
 struct Layout {
-    size_t kscale, albedo, g, L0, kscale_f, albedo_f, g_f, L0_f, offsets, ins, ledger, oof, counters, err, queue, total;
+    size_t kscale, albedo, g, L0, kscale_f, albedo_f, g_f, L0_f, offsets, first, ins, ledger, oof, counters, err, queue, total;
     size_t zero_begin, zero_bytes;  // accumulators zeroed every call
 };
 
@@ -87,6 +87,7 @@ Layout make_layout(int NL, int ninstr)
     l.g_f = take(sizeof(float) * NL);
     l.L0_f = take(sizeof(float) * NL);
     l.offsets = take(sizeof(unsigned long long) * (NL + 1));
+    l.first = take(sizeof(unsigned long long) * NL);
     l.ins = take(sizeof(InstrDev) * (ninstr > 0 ? ninstr : 1));
     l.ledger = take(sizeof(double) * 4 * NL);
     l.oof = take(sizeof(double) * (size_t)(ninstr > 0 ? ninstr : 1) * NL);
@@ -305,6 +306,15 @@ int validate(skirt_grid_t g, const skirt_source* src, const skirt_wavelengths* w
         if (wl->lsrc && (!std::isfinite(wl->lsrc[j]) || wl->lsrc[j] < 0))
             return fail(SKIRT_ERR_INVALID_ARG, "lsrc[%d] invalid", j);
         if (npk[j] >= (1ull << 32)) return fail(SKIRT_ERR_INVALID_ARG, "npackets[%d] must be < 2^32", j);
+        const uint64_t first = opts && opts->first_packet ? opts->first_packet[j] : 0;
+        if (first > (1ull << 32) - npk[j])
+            return fail(SKIRT_ERR_INVALID_ARG, "first_packet[%d] + npackets[%d] must not exceed 2^32", j, j);
+        if (opts && opts->total_packets) {
+            const uint64_t tot = opts->total_packets[j];
+            if (tot >= (1ull << 32) || first + npk[j] > tot)
+                return fail(SKIRT_ERR_INVALID_ARG,
+                            "first_packet[%d] + npackets[%d] must not exceed total_packets[%d] (< 2^32)", j, j, j);
+        }
     }
     P.offsets.assign(P.NL + 1, 0);
     for (int j = 0; j < P.NL; ++j) P.offsets[j + 1] = P.offsets[j] + npk[j];
@@ -408,13 +418,18 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
         h_ks[j] = wl->kscale[j];
         h_al[j] = wl->albedo[j];
         h_g[j] = wl->g[j];
-        h_L0[j] = npk[j] ? lsrc[j] / (double)npk[j] : 0.0;
+        const uint64_t ntot = opts->total_packets ? opts->total_packets[j] : npk[j];
+        h_L0[j] = npk[j] ? lsrc[j] / (double)ntot : 0.0;
         h_ksf[j] = (float)h_ks[j];
         h_alf[j] = (float)h_al[j];
         h_gf[j] = (float)h_g[j];
         h_L0f[j] = (float)h_L0[j];
     }
     std::memcpy(hp + L.offsets, P.offsets.data(), sizeof(unsigned long long) * (NL + 1));
+    {
+        unsigned long long* h_first = (unsigned long long*)(hp + L.first);
+        for (int j = 0; j < NL; ++j) h_first[j] = opts->first_packet ? opts->first_packet[j] : 0;
+    }
     InstrDev* h_ins = (InstrDev*)(hp + L.ins);
     {
         long long off = 0;
@@ -488,6 +503,7 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
         A.hi_f[a] = (float)g->bbox[2 * a + 1];
     }
     A.offsets = (const unsigned long long*)(dp + L.offsets);
+    A.pk_first = (const unsigned long long*)(dp + L.first);
     A.total = P.total;
     A.src_kind = src->kind;
     for (int a = 0; a < 3; ++a) {
@@ -673,15 +689,20 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
 // ------------------------------------------------------------------------ autotune
 extern "C" int skirt_autotune(skirt_grid_t g, const skirt_source* src, const skirt_wavelengths* wl,
                               const uint64_t* npk, uint64_t seed, const skirt_instrument* ins, int ninstr,
-                              skirt_trace_opts* opts, double frac, double* absorbed, double* images,
-                              double* sed, void* stream)
+                              skirt_trace_opts* opts, double frac, int repeats, double* absorbed, double* images,
+                              double* sed, skirt_tune_report* report, void* stream)
 {
-    if (!opts || !wl || !npk) return fail(SKIRT_ERR_INVALID_ARG, "opts / wl / npackets is NULL");
+    if (!g || !opts || !wl || !npk) return fail(SKIRT_ERR_INVALID_ARG, "grid / opts / wl / npackets is NULL");
     if (!(frac > 0 && frac <= 1)) return fail(SKIRT_ERR_INVALID_ARG, "sample_fraction must be in (0, 1]");
+    if (wl->n < 1 || wl->n > 65536) return fail(SKIRT_ERR_INVALID_ARG, "wavelength count %d out of range", wl->n);
+    if (repeats <= 0) repeats = 2;
+    if (repeats > 16) return fail(SKIRT_ERR_INVALID_ARG, "repeats must be <= 16");
     std::vector<uint64_t> sample(wl->n);
+    unsigned long long nsample = 0;
     for (int j = 0; j < wl->n; ++j) {
         uint64_t n = (uint64_t)std::llround((double)npk[j] * frac);
         sample[j] = (npk[j] > 0 && n == 0) ? 1 : n;
+        nsample += sample[j];
     }
     skirt_trace_opts o = *opts;
     o.schedule = SKIRT_SCHED_PERSISTENT;
@@ -689,44 +710,79 @@ extern "C" int skirt_autotune(skirt_grid_t g, const skirt_source* src, const ski
     o.accumulate = 0;
     o.nrec = 0;
     o.records = nullptr;
+    o.first_packet = nullptr;
+    o.total_packets = nullptr;
     const bool mixed = o.precision == SKIRT_PREC_MIXED;
-    const int blocks[4] = {64, 128, 256, mixed ? 256 : 512};
+    const bool oct = g->oct_levels > 0;
+
+    // the candidates: the requested schedule (defaults resolved), then the sweep
+    std::vector<skirt_tune_point> cand;
+    {
+        skirt_tune_point p{};
+        p.block = o.block > 0 ? o.block : 256;
+        p.chunk = o.chunk > 0 ? o.chunk : 4;
+        p.step_min = o.step_min > 0 ? o.step_min : 20;
+        int maxbps = 0;
+        CK(trace_occupancy(o.precision, p.block, &maxbps, oct));
+        p.blocks_per_sm = o.blocks_per_sm > 0 ? o.blocks_per_sm : (maxbps > 0 ? maxbps : 1);
+        cand.push_back(p);
+    }
+    const int blocks[4] = {64, 128, 256, 512};
     const int chunks[3] = {1, 4, 16};
     const int step_mins[3] = {16, 20, 24};
-    float best = 1e30f;
-    int bb = 256, bc = 4, bbps = 0, bsm = 20;
-    for (int bi = 0; bi < 4; ++bi) {
-        if (bi > 0 && blocks[bi] == blocks[bi - 1]) continue;
+    for (int bi = 0; bi < (mixed ? 3 : 4); ++bi) {
         int maxbps = 0;
-        CK(trace_occupancy(o.precision, blocks[bi], &maxbps, g->oct_levels > 0));
+        CK(trace_occupancy(o.precision, blocks[bi], &maxbps, oct));
         if (maxbps < 1) continue;
-        for (int ci = 0; ci < 3; ++ci) {
-            for (int si = 0; si < (mixed ? 3 : 1); ++si) {
+        for (int ci = 0; ci < 3; ++ci)
+            for (int si = 0; si < (mixed ? 3 : 1); ++si)
                 for (int bps = maxbps; bps >= 1; bps = (bps > 1 ? (bps + 1) / 2 : 0)) {
-                    o.block = blocks[bi];
-                    o.chunk = chunks[ci];
-                    o.step_min = step_mins[si];
-                    o.blocks_per_sm = bps;
-                    skirt_ledger led;
-                    int r = skirt_trace(g, src, wl, sample.data(), seed, ins, ninstr, &o, absorbed, images, sed,
-                                        &led, nullptr, stream);
-                    if (r && r != SKIRT_ERR_EVENT_CAP) return r;
-                    if (led.kernel_ms > 0 && led.kernel_ms < best) {
-                        best = led.kernel_ms;
-                        bb = blocks[bi];
-                        bc = chunks[ci];
-                        bbps = bps;
-                        bsm = step_mins[si];
-                    }
+                    skirt_tune_point p{blocks[bi], chunks[ci], bps, mixed ? step_mins[si] : 20, 0.f};
+                    const skirt_tune_point& d = cand[0];
+                    const bool same = p.block == d.block && p.chunk == d.chunk && p.blocks_per_sm == d.blocks_per_sm &&
+                                      (!mixed || p.step_min == d.step_min);
+                    if (!same && (int)cand.size() < SKIRT_TUNE_MAX_POINTS) cand.push_back(p);
                     if (bps == 1) break;
                 }
-            }
+    }
+    auto run = [&](const skirt_tune_point& p, float* ms) -> int {
+        o.block = p.block;
+        o.chunk = p.chunk;
+        o.blocks_per_sm = p.blocks_per_sm;
+        o.step_min = p.step_min;
+        skirt_ledger led;
+        int r = skirt_trace(g, src, wl, sample.data(), seed, ins, ninstr, &o, absorbed, images, sed, &led, nullptr,
+                            stream);
+        if (r && r != SKIRT_ERR_EVENT_CAP) return r;
+        *ms = led.kernel_ms > 0 ? led.kernel_ms : 1e30f;
+        return SKIRT_OK;
+    };
+    float warm = 0.f;
+    if (int r = run(cand[0], &warm)) return r;
+    for (auto& p : cand) {
+        p.ms = 1e30f;
+        for (int k = 0; k < repeats; ++k) {
+            float ms = 0.f;
+            if (int r = run(p, &ms)) return r;
+            if (ms < p.ms) p.ms = ms;
         }
     }
-    opts->block = bb;
-    opts->chunk = bc;
-    opts->blocks_per_sm = bbps;
-    opts->step_min = bsm;
+    int best = 0;
+    for (int i = 1; i < (int)cand.size(); ++i)
+        if (cand[i].ms < cand[best].ms) best = i;
+    const int chosen = cand[best].ms < 0.98f * cand[0].ms ? best : 0;
+    opts->block = cand[chosen].block;
+    opts->chunk = cand[chosen].chunk;
+    opts->blocks_per_sm = cand[chosen].blocks_per_sm;
+    if (mixed) opts->step_min = cand[chosen].step_min;
+    if (report) {
+        std::memset(report, 0, sizeof *report);
+        report->n = (int)cand.size();
+        report->chosen = chosen;
+        report->repeats = repeats;
+        report->sample_packets = nsample;
+        for (size_t i = 0; i < cand.size(); ++i) report->points[i] = cand[i];
+    }
     // leave the outputs zeroed
     skirt_trace_opts z = o;
     std::vector<uint64_t> none(wl->n, 0);

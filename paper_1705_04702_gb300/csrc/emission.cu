@@ -797,10 +797,14 @@ extern "C" int skirt_dust_emission_exact_static(const double* absorbed, long lon
             g_static_ptr[dev] = (double*)p;
         }
         shares = g_static_ptr[dev];
-        // the table is rewritten in full by every call (no part needs zeroing); a copy from
-        // pageable memory has left the host buffer when cudaMemcpyAsync returns
+        // the table is rewritten in full by every call (no part needs zeroing).  The copy
+        // reads the shared host buffer, so it has to finish before another thread may
+        // refill that buffer: the stream is synchronised before the lock is released
+        // (CUDA does not promise that an asynchronous copy from pageable memory has
+        // read its source when the call returns).
         fill_shares(lambda_in, n_in, g_static_host);
         ECK(cudaMemcpyAsync(shares, g_static_host, sizeof(double) * NPOP * n_in, cudaMemcpyHostToDevice, s));
+        ECK(cudaStreamSynchronize(s));
     }
     int rc = launch_exact_emission(absorbed, n_in, shares, mass, nullptr, ncell, emission, temperature, s);
     ECK(cudaStreamSynchronize(s));

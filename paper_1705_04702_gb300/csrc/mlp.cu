@@ -778,8 +778,46 @@ struct Work {
     }
     void release(cudaStream_t s)
     {
-        for (float* p : {xb, tb, z1, a1, z2, a2, z3, d3, da, d, loss, part})
-            if (p) cudaFreeAsync(p, s);
+        for (float** p : {&xb, &tb, &z1, &a1, &z2, &a2, &z3, &d3, &da, &d, &loss, &part}) {
+            if (*p) cudaFreeAsync(*p, s);
+            *p = nullptr;
+        }
+    }
+};
+
+// Everything a training call acquires, released on every return path (the
+// stream-ordered frees go on the caller's stream, after the private stream's
+// work has been joined to it).
+struct TrainScope {
+    cudaStream_t s = nullptr;
+    Work w;
+    float* target = nullptr;
+    double* d_st = nullptr;
+    unsigned long long* d_ab = nullptr;
+    float* d_sched = nullptr;
+    long long* d_t = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ready = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    explicit TrainScope(cudaStream_t st) : s(st) {}
+    ~TrainScope()
+    {
+        if (cs) {
+            if (ready && cudaEventRecord(ready, cs) == cudaSuccess) cudaStreamWaitEvent(s, ready, 0);
+            cudaStreamSynchronize(cs);
+        }
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cs) cudaStreamDestroy(cs);
+        if (ready) cudaEventDestroy(ready);
+        w.release(s);
+        if (target) cudaFreeAsync(target, s);
+        if (d_st) cudaFreeAsync(d_st, s);
+        if (d_ab) cudaFreeAsync(d_ab, s);
+        if (d_sched) cudaFreeAsync(d_sched, s);
+        if (d_t) cudaFreeAsync(d_t, s);
+        cudaGetLastError();
     }
 };
 
@@ -838,7 +876,8 @@ extern "C" int skirt_mlp_grad(skirt_mlp_t net, const float* x_std, const float* 
 {
     if (!net || !x_std || !target || n < 1) return set_error(SKIRT_ERR_INVALID_ARG, "net / x_std / target / n");
     cudaStream_t s = (cudaStream_t)stream;
-    Work w;
+    TrainScope sc(s);
+    Work& w = sc.w;
     MCK(w.alloc(n, s));
     MCK(cudaMemcpyAsync(w.xb, x_std, sizeof(float) * n * NIN, cudaMemcpyDefault, s));
     MCK(cudaMemcpyAsync(w.tb, target, sizeof(float) * n * NO, cudaMemcpyDefault, s));
@@ -848,7 +887,6 @@ extern "C" int skirt_mlp_grad(skirt_mlp_t net, const float* x_std, const float* 
     if (grad) MCK(cudaMemcpyAsync(grad, net->G, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, s));
     float l = 0.f;
     MCK(cudaMemcpyAsync(&l, w.loss, sizeof(float), cudaMemcpyDeviceToHost, s));
-    w.release(s);
     MCK(cudaStreamSynchronize(s));
     if (loss) *loss = l;
     return SKIRT_OK;
@@ -862,20 +900,20 @@ extern "C" int skirt_mlp_train(skirt_mlp_t net, const float* features, const dou
     if (B < 32 || B > (1 << 16) || n < B) return set_error(SKIRT_ERR_INVALID_ARG, "batch must be in [32, 65536] and <= n");
     if (opts->epochs < 1 || !(opts->lr > 0)) return set_error(SKIRT_ERR_INVALID_ARG, "epochs / lr invalid");
     cudaStream_t s = (cudaStream_t)stream;
+    TrainScope sc(s);
     // target shapes: every emission row normalised to sum 1
-    float* target = nullptr;
+    float*& target = sc.target;
     MCK(cudaMallocAsync((void**)&target, sizeof(float) * NO * (size_t)n, s));
     normalize_rows_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(emission, target, n);
     MCK(cudaGetLastError());
     // standardisation and hull from the training features
-    double* d_st = nullptr;
+    double*& d_st = sc.d_st;
     MCK(cudaMallocAsync((void**)&d_st, sizeof(double) * 4 * NIN, s));
     feature_stats_kernel<<<NIN, 256, 0, s>>>(features, n, d_st);
     MCK(cudaGetLastError());
     double st[4 * NIN];
     MCK(cudaMemcpyAsync(st, d_st, sizeof st, cudaMemcpyDeviceToHost, s));
     MCK(cudaStreamSynchronize(s));
-    cudaFreeAsync(d_st, s);
     for (int k = 0; k < NIN; ++k) {
         const double mean = st[4 * k] / (double)n;
         const double var = st[4 * k + 1] / (double)n - mean * mean;
@@ -887,7 +925,7 @@ extern "C" int skirt_mlp_train(skirt_mlp_t net, const float* features, const dou
     if (int r = upload_stats(net)) return r;
     MCK(cudaMemsetAsync(net->Mo, 0, sizeof(float) * NPARAM, s));
     MCK(cudaMemsetAsync(net->Vo, 0, sizeof(float) * NPARAM, s));
-    Work w;
+    Work& w = sc.w;
     MCK(w.alloc(B, s));
     const long long steps = n / B;
     const long long total_steps = steps * opts->epochs;
@@ -913,9 +951,9 @@ extern "C" int skirt_mlp_train(skirt_mlp_t net, const float* features, const dou
         sched[3 * t + 1] = 1.f - std::pow(opts->beta1, (float)(t + 1));
         sched[3 * t + 2] = 1.f - std::pow(opts->beta2, (float)(t + 1));
     }
-    unsigned long long* d_ab = nullptr;
-    float* d_sched = nullptr;
-    long long* d_t = nullptr;
+    unsigned long long*& d_ab = sc.d_ab;
+    float*& d_sched = sc.d_sched;
+    long long*& d_t = sc.d_t;
     MCK(cudaMallocAsync((void**)&d_ab, sizeof(unsigned long long) * ab.size(), s));
     MCK(cudaMallocAsync((void**)&d_sched, sizeof(float) * sched.size(), s));
     MCK(cudaMallocAsync((void**)&d_t, sizeof(long long), s));
@@ -925,14 +963,14 @@ extern "C" int skirt_mlp_train(skirt_mlp_t net, const float* features, const dou
 
     // one training step (gather, forward, backward, Adam, step counter) as a
     // CUDA graph, captured on a private stream and replayed for every step
-    cudaStream_t cs = nullptr;
+    cudaStream_t& cs = sc.cs;
     MCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    cudaEvent_t ready = nullptr;
+    cudaEvent_t& ready = sc.ready;
     MCK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
     MCK(cudaEventRecord(ready, s));
     MCK(cudaStreamWaitEvent(cs, ready, 0));
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t& graph = sc.graph;
+    cudaGraphExec_t& gexec = sc.gexec;
     int rc = SKIRT_OK;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
@@ -958,24 +996,10 @@ extern "C" int skirt_mlp_train(skirt_mlp_t net, const float* features, const dou
         }
         if (e != cudaSuccess) rc = set_error(SKIRT_ERR_CUDA, "training step: %s", cudaGetErrorString(e));
     }
-    cudaEventRecord(ready, cs);
-    cudaStreamWaitEvent(s, ready, 0);
-    if (gexec) cudaGraphExecDestroy(gexec);
-    if (graph) cudaGraphDestroy(graph);
-    cudaStreamSynchronize(cs);
-    cudaStreamDestroy(cs);
-    cudaEventDestroy(ready);
-    cudaFreeAsync(d_ab, s);
-    cudaFreeAsync(d_sched, s);
-    cudaFreeAsync(d_t, s);
-    if (rc) {
-        w.release(s);
-        cudaFreeAsync(target, s);
-        cudaStreamSynchronize(s);
-        return rc;
-    }
-    w.release(s);
-    cudaFreeAsync(target, s);
+    if (rc) return rc;  // the scope joins the private stream and frees everything
+    // join the private stream before the repack on the caller's stream
+    MCK(cudaEventRecord(ready, cs));
+    MCK(cudaStreamWaitEvent(s, ready, 0));
     if (int r = repack(net, s)) return r;
     MCK(cudaStreamSynchronize(s));
     return SKIRT_OK;

@@ -83,6 +83,7 @@ struct TraceArgs {
     float hi_f[3];
     float w_min_f;
     const unsigned long long* offsets;     // [nlambda + 1] prefix sums of packet counts
+    const unsigned long long* pk_first;    // [nlambda] stream index of each wavelength's first packet
     unsigned long long total;
     int src_kind;
     double src_pos[3], src_dir[3], h_R, h_z;

@@ -62,10 +62,8 @@ __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     InstrDev* sins = reinterpret_cast<InstrDev*>(smem_raw);
-    double* wbuf_all = reinterpret_cast<double*>(smem_raw + sizeof(InstrDev) * A.ninstr);
     for (int i = threadIdx.x; i < A.ninstr; i += blockDim.x) sins[i] = A.ins[i];
     __syncthreads();
-    double* wbuf = wbuf_all + (threadIdx.x & ~31);
 
     const int NL = A.nlambda;
     const int nx = A.nx, ny = A.ny, nz = A.nz;
@@ -313,7 +311,7 @@ __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A)
                     led_lam = lam;
                 }
             }
-            pk = (uint32_t)(qq - __ldg(A.offsets + lam));
+            pk = (uint32_t)(qq - __ldg(A.offsets + lam) + __ldg(A.pk_first + lam));
             L = L0;
             p_esc = p_abs = p_res = p_peel = 0.0;
             ev = 0;
@@ -462,9 +460,9 @@ __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A)
                 const R fb = P<R>::floorr((b + P<R>::half_fov(I)) * P<R>::inv_dpx(I));
                 if (fa >= (R)0 && fa < (R)I.npx && fb >= (R)0 && fb < (R)I.npx) {
                     const long long pix = (long long)fb * I.npx + (long long)fa;
-                    red_agg(A.images + I.img_off + pix * NL + lam, flux, wbuf);
+                    atomicAdd(A.images + I.img_off + pix * NL + lam, flux);
                 } else {
-                    red_agg(A.oof + (size_t)peel_i * NL + lam, flux, wbuf);
+                    atomicAdd(A.oof + (size_t)peel_i * NL + lam, flux);
                 }
             }
             ++peel_i;
@@ -509,8 +507,9 @@ __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A)
         l_esc += p_esc;
         l_res += p_res;
         if (!isfinite(p_esc + p_abs + p_res + p_peel)) atomicOr(A.err, (unsigned)ERRBIT_NONFINITE);
-        if (pk < (uint32_t)A.nrec) {
-            double* rec = A.records + ((size_t)lam * A.nrec + pk) * SKIRT_REC_FIELDS;
+        const uint32_t li = pk - (uint32_t)__ldg(A.pk_first + lam);  // index within this call
+        if (li < (uint32_t)A.nrec) {
+            double* rec = A.records + ((size_t)lam * A.nrec + li) * SKIRT_REC_FIELDS;
             rec[0] = (double)nscat;
             rec[1] = p_esc;
             rec[2] = p_abs;
@@ -567,7 +566,14 @@ __global__ void f32_to_f64_kernel(const float* __restrict__ in, double* __restri
 
 }  // namespace
 
-size_t trace_smem_bytes(int ninstr, int block) { return sizeof(InstrDev) * (size_t)ninstr + sizeof(double) * (size_t)block; }
+// The FP64 form keeps only the instruments in shared memory.  Its lanes run
+// independent state machines with no point where the warp is known to be
+// converged, so its peel-off tallies are plain reductions.
+size_t trace_smem_bytes(int ninstr, int block)
+{
+    (void)block;
+    return sizeof(InstrDev) * (size_t)ninstr;
+}
 
 cudaError_t launch_trace(const TraceArgs& a, int precision, int block, int grid, cudaStream_t s)
 {

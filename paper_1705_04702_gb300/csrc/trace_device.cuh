@@ -19,30 +19,26 @@ enum {
     ST_END_PACKET,
 };
 
-// Warp-aggregated FP64 reduction: lanes of the converged group that target
-// the same address combine their values through shared memory (one slot per
-// lane) and one lane issues a single red.global.add.f64.
-__device__ __forceinline__ void red_agg(double* addr, double v, double* wbuf)
+// Warp-aggregated FP64 reduction of at most one pending tally per lane: the
+// lane's target address in `addr` (nullptr: none) and its value in
+// wbuf[lane].  All 32 lanes of the warp call it together, so the full-warp
+// masks of the ballot and the match are exact.  Lanes with the same address
+// add their values through shared memory (in lane order) and the lowest of
+// them issues a single red.global.add.f64; every lane's addr is cleared.
+__device__ __forceinline__ void warp_tally_flush(double*& addr, double* wbuf)
 {
-    const unsigned active = __activemask();
-    const unsigned peers = __match_any_sync(active, (unsigned long long)addr);
+    const unsigned pend = __ballot_sync(0xffffffffu, addr != nullptr);
+    if (!pend) return;
+    __syncwarp();
+    const unsigned peers = __match_any_sync(0xffffffffu, (unsigned long long)addr);
     const int lane = threadIdx.x & 31;
-    if (peers == (1u << lane)) {
-        atomicAdd(addr, v);
-        return;
-    }
-    wbuf[lane] = v;
-    __syncwarp(peers);
-    if (lane == __ffs(peers) - 1) {
+    if (addr && lane == __ffs(peers) - 1) {
         double s = 0.0;
-        unsigned p = peers;
-        while (p) {
-            s += wbuf[__ffs(p) - 1];
-            p &= p - 1;
-        }
+        for (unsigned p = peers; p; p &= p - 1) s += wbuf[__ffs(p) - 1];
         atomicAdd(addr, s);
     }
-    __syncwarp(peers);
+    addr = nullptr;
+    __syncwarp();
 }
 
 // Henyey-Greenstein phase function, normalised to average 1 over the sphere.

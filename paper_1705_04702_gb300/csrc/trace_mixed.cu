@@ -197,6 +197,7 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
     float k0 = 0.f, k1 = 0.f, k2 = 0.f;
     bool have_pc = false;
     int pc0 = 0, pc1 = 0, pc2 = 0;
+    double* tally = nullptr;  // pending peel-off tally (value in wbuf[lane]), flushed per warp
 
     auto axis_cell = [&](float xh, float xl, float lo, float d, int n, const float2* f) {
         int c = (int)fminf(fmaxf(floorf((xh - lo) / d), 0.f), (float)(n - 1));
@@ -488,7 +489,7 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                 lam = ll;
                 krs = __ldg(A.kscale_f + lam);
                 gg = __ldg(A.g_f + lam);
-                C.pk[t] = (unsigned)(qq - __ldg(A.offsets + lam));
+                C.pk[t] = (unsigned)(qq - __ldg(A.offsets + lam) + __ldg(A.pk_first + lam));
                 L = C.L0[t];
                 C.p_esc[t] = C.p_abs[t] = C.p_res[t] = C.p_peel[t] = 0.f;
                 C.ev[t] = 0;
@@ -670,12 +671,21 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                     const float fa = floorf((a + I.half_fov_f) * I.inv_dpx_f);
                     const float fb = floorf((b + I.half_fov_f) * I.inv_dpx_f);
                     if (flux >= 1.17549435e-38f) {
+                        // the pixel's tally (or the out-of-frame one) is added after the event
+                        // phase, where the whole warp aggregates its lanes' tallies
+                        double* addr;
                         if (fa >= 0.f && fa < (float)I.npx && fb >= 0.f && fb < (float)I.npx) {
                             const long long pix = (long long)fb * I.npx + (long long)fa;
-                            red_agg(A.images + I.img_off + pix * NL + lam, f2d(flux), wbuf);
+                            addr = A.images + I.img_off + pix * NL + lam;
                         } else {
-                            red_agg(A.oof + (size_t)pi * NL + lam, f2d(flux), wbuf);
+                            addr = A.oof + (size_t)pi * NL + lam;
                         }
+                        // a lane tallies at most once per event phase (every tally ends a
+                        // peel-off traversal and the next step begins one); a second tally
+                        // would be added at once
+                        if (tally) atomicAdd(tally, wbuf[t & 31]);
+                        wbuf[t & 31] = f2d(flux);
+                        tally = addr;
                     }
                 }
                 C.peel_i[t] = pi + 1;
@@ -711,7 +721,7 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
             C.l_esc[t] += f2d(pe);
             C.l_res[t] += f2d(pr);
             if (!isfinite(pe + pa + pr + pp)) atomicOr(A.err, (unsigned)ERRBIT_NONFINITE);
-            const unsigned pk = C.pk[t];
+            const unsigned pk = C.pk[t] - (unsigned)__ldg(A.pk_first + lam);  // index within this call
             if (pk < (unsigned)A.nrec) {
                 double* rec = A.records + ((size_t)lam * A.nrec + pk) * SKIRT_REC_FIELDS;
                 rec[0] = (double)C.nscat[t];
@@ -744,6 +754,7 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
             continue;
         }
         if (!stepping && alive) events();
+        warp_tally_flush(tally, wbuf);  // all 32 lanes reach this point together
     }
 
     flush_ledger();

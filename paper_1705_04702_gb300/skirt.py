@@ -45,7 +45,27 @@ class skirt_trace_opts(ctypes.Structure):
                 ("block", ctypes.c_int), ("chunk", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("step_min", ctypes.c_int), ("phase", ctypes.c_uint32),
                 ("nrec", ctypes.c_int),
-                ("records", ctypes.c_void_p)]
+                ("records", ctypes.c_void_p),
+                ("first_packet", ctypes.POINTER(ctypes.c_uint64)),
+                ("total_packets", ctypes.POINTER(ctypes.c_uint64))]
+
+
+TUNE_MAX_POINTS = 256
+
+
+class skirt_tune_point(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int), ("chunk", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("step_min", ctypes.c_int), ("ms", ctypes.c_float)]
+
+
+class skirt_tune_report(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("chosen", ctypes.c_int), ("repeats", ctypes.c_int),
+                ("sample_packets", ctypes.c_ulonglong), ("points", skirt_tune_point * TUNE_MAX_POINTS)]
+
+    def as_dict(self):
+        pts = [{k: getattr(self.points[i], k) for k, _ in skirt_tune_point._fields_} for i in range(self.n)]
+        return {"n": self.n, "chosen": self.chosen, "repeats": self.repeats, "sample_packets": self.sample_packets,
+                "points": pts}
 
 
 class skirt_ledger(ctypes.Structure):
@@ -82,7 +102,8 @@ def _load():
     L.skirt_trace.restype = i
     L.skirt_autotune.argtypes = [vp, ctypes.POINTER(skirt_source), ctypes.POINTER(skirt_wavelengths),
                                  ctypes.POINTER(u64), u64, ctypes.POINTER(skirt_instrument), i,
-                                 ctypes.POINTER(skirt_trace_opts), ctypes.c_double, vp, vp, vp, vp]
+                                 ctypes.POINTER(skirt_trace_opts), ctypes.c_double, i, vp, vp, vp,
+                                 ctypes.POINTER(skirt_tune_report), vp]
     L.skirt_autotune.restype = i
     L.skirt_microbench.argtypes = [i, ctypes.c_longlong, _dp, ctypes.POINTER(ctypes.c_float)]
     L.skirt_philox4x32_10.argtypes = [vp, vp, vp, i]
@@ -169,16 +190,18 @@ def skirt_trace(grid, src: skirt_source, wl: skirt_wavelengths, npackets, seed, 
 
 
 def skirt_autotune(grid, src, wl, npackets, seed, instruments, opts, sample_fraction, absorbed, images, sed,
-                   stream=None):
+                   stream=None, repeats=0):
+    """Writes the tuned schedule into opts; returns the sweep report (dict)."""
     npk = np.ascontiguousarray(npackets, dtype=np.uint64)
     ins_arr = (skirt_instrument * max(len(instruments), 1))(*instruments)
     st = None if stream is None else ctypes.c_void_p(int(stream))
+    rep = skirt_tune_report()
     code = lib.skirt_autotune(grid, ctypes.byref(src), ctypes.byref(wl),
                               npk.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), int(seed) & (2 ** 64 - 1),
-                              ins_arr, len(instruments), ctypes.byref(opts), float(sample_fraction),
-                              _ptr(absorbed), _ptr(images), _ptr(sed), st)
+                              ins_arr, len(instruments), ctypes.byref(opts), float(sample_fraction), int(repeats),
+                              _ptr(absorbed), _ptr(images), _ptr(sed), ctypes.byref(rep), st)
     _check(code, "skirt_autotune", (ERR_EVENT_CAP,))
-    return opts
+    return rep.as_dict()
 
 
 def skirt_philox4x32_10(ctr, key):
@@ -254,12 +277,24 @@ class Grid:
             pass
 
 
+def packet_range_arrays(first_packet, total_packets):
+    """uint64 arrays for skirt_trace_opts.first_packet / total_packets (None stays None)."""
+    f = None if first_packet is None else np.ascontiguousarray(first_packet, dtype=np.uint64)
+    t = None if total_packets is None else np.ascontiguousarray(total_packets, dtype=np.uint64)
+    return f, t
+
+
+def _u64p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+
+
 def run_problem(prob, grid: Grid | None = None, precision=PREC_MIXED, schedule=SCHED_PERSISTENT, nrec=0,
                 use_graph=False, peel=True, block=0, chunk=0, blocks_per_sm=0, step_min=0, outputs=None, emission=None,
-                device="cuda", stream=None, accumulate=False):
+                device="cuda", stream=None, accumulate=False, first_packet=None, total_packets=None):
     """Traces a workloads.Problem on the GPU; returns a dict of torch tensors
     (absorbed [ncell, n], images list [npx, npx, n], sed [ninstr, n], records)
-    plus ledger information."""
+    plus ledger information.  first_packet / total_packets (per wavelength)
+    select a packet range of the run, as in skirt_trace_opts."""
     import torch
     own = grid is None
     if own:
@@ -290,6 +325,9 @@ def run_problem(prob, grid: Grid | None = None, precision=PREC_MIXED, schedule=S
     o.phase = prob.phase
     o.nrec = nrec
     o.records = records.data_ptr() if records is not None else None
+    fp, tp = packet_range_arrays(first_packet, total_packets)
+    o.first_packet = _u64p(fp)
+    o.total_packets = _u64p(tp)
     src = make_source(prob.source, emission)
     code, led, per = skirt_trace(grid.h, src, tables.c, prob.npk, prob.seed, ins, o, absorbed, images, sed,
                                  stream=stream)

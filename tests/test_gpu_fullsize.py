@@ -10,7 +10,8 @@ import pytest
 
 from paper_1705_04702_gb300 import workloads as W
 
-from parity import REL_MIXED_PACKET, compare_records
+from parity import (REL_MIXED_PACKET, REL_MIXED_TALLY, compare_records, compare_tally, rebin, rebin_factor,
+                    record_sigma_check, scattering_counts_agree, unmatched)
 
 pytestmark = pytest.mark.gpu
 
@@ -56,11 +57,62 @@ def test_disk_1e8_packets_sampled(S, oracle_lib):
     assert 0.3 * F < float(g["sed"][0, 0]) < 1.5 * F
 
 
-def _check_full(S, oracle_lib, prob, nrec, min_match, same_n_min=0.999):
+def test_disk_1e7_packets_full_grid(S):
+    """The bench's workload and launch configuration (mixed form, persistent
+    launch from a CUDA graph) at 1e7 packets against the oracle run over the
+    same packets on every host core: every absorbed cell and every rebinned
+    pixel block holding >= 1e-4 of its table's total within 1e-4, the
+    L1-normalised differences within 1e-4, SEDs and ledger within 1e-4."""
+    from oracle_pool import trace_all_cores
+    n = 10_000_000
+    spec = {"maker": "disk_problem", "kwargs": {"npackets": n, "n": 256, "nlambda": 1, "npx": 512}}
+    ref = trace_all_cores(spec, n)
+    prob = W.disk_problem(n, n=256, nlambda=1, npx=512)
+    g = S.run_problem(prob, precision=S.PREC_MIXED, schedule=S.SCHED_PERSISTENT, use_graph=True)
+    assert g["status"] == S.OK and ref["status"] == 0
+    ga = g["absorbed"].cpu().numpy()
+    report = {"oracle_cores": ref["cores"]}
+    fails = []
+
+    def check(name, fn):
+        try:
+            report[name] = fn()
+        except AssertionError as e:
+            fails.append((name, str(e)[:300]))
+
+    check("absorbed_l1", lambda: compare_tally(ga, ref["absorbed"], REL_MIXED_TALLY, significant=1e-4))
+    off = 0
+    for q, ins in enumerate(prob.instruments):
+        k = ins.npx * ins.npx
+        gi = g["images"][q].cpu().numpy()
+        ri = ref["images"][off:off + k].reshape(ins.npx, ins.npx, 1)
+        off += k
+        b = rebin_factor(prob, ins)
+        report[f"image{q}_bin"] = b
+        check(f"image{q}_l1", lambda gi=gi, ri=ri, b=b: compare_tally(rebin(gi, b), rebin(ri, b), REL_MIXED_TALLY,
+                                                                        significant=1e-4))
+    check("sed", lambda: compare_tally(g["sed"].cpu().numpy(), ref["sed"], REL_MIXED_TALLY, significant=0.0))
+    check("ledger", lambda: np.testing.assert_allclose(g["ledger_per_lambda"], ref["ledger"], rtol=REL_MIXED_TALLY))
+    print(report, fails)
+    assert not fails, fails
+
+
+def _check_full(S, oracle_lib, prob, nrec, min_match=0.999, same_n_min=0.999, chaotic=False):
     g = S.run_problem(prob, precision=S.PREC_MIXED, schedule=S.SCHED_PERSISTENT, nrec=nrec, use_graph=True)
     r = oracle_lib.trace(prob, 0, nrec, nrec=nrec)
-    compare_records(g["records"].cpu().numpy(), r["records"], prob, REL_MIXED_PACKET, min_match,
-                    same_n_min=same_n_min)
+    gr = g["records"].cpu().numpy()
+    sample = prob.with_packets(np.minimum(prob.npk, nrec))
+    if chaotic:
+        # diverged histories are other Monte Carlo samples of the same process:
+        # the scattering counts follow the oracle's distribution, and the
+        # unmatched packets' shares of the ledger and SEDs differ by at most
+        # K_SIGMA standard deviations
+        p = scattering_counts_agree(gr, r["records"], sample)
+        um = unmatched(gr, r["records"], sample, REL_MIXED_PACKET)
+        record_sigma_check(gr, r["records"], sample, um)
+        print("chi2 p", p, "unmatched", um.mean())
+    else:
+        compare_records(gr, r["records"], prob, REL_MIXED_PACKET, min_match, same_n_min=same_n_min)
     led = g["ledger"]
     assert g["status"] == S.OK and led["status_bits"] == 0
     # every wavelength launched its full luminosity (lsrc = 1 per wavelength)
@@ -84,15 +136,14 @@ def test_torus_batched_full_sampled(S, oracle_lib):
     """The batched form at scale: the clumpy torus, 200 wavelengths with
     uneven counts (7.5e8 packets) in one persistent graph launch.  The
     single-cell clumps (100x density) amplify FP32 rounding differences from
-    event to event, more so the finer the grid: at 256^3 about 1.1% of the
-    ~20-scattering histories fork (0.5% at 128^3, 0.07% at 48^3), while the
-    FP64 form follows the oracle exactly (next test).  So 98.5% of the sampled
-    packets must take the same number of scatterings, and 80% must agree
-    within 1e-5 in every record field (measured 83%: the final position after
-    ~20 scatterings is the first field to drift; 93% at 48^3)."""
+    event to event, more so the finer the grid, while the FP64 form follows
+    the oracle exactly (next test).  The sampled packets (the first 60 of
+    every wavelength) are checked statistically: scattering-count
+    distribution, and the unmatched packets' ledger and SED shares within
+    K_SIGMA."""
     prob = W.torus_problem(n=256, nlambda=200, npx=512)
     assert prob.total_packets > 5e8
-    _check_full(S, oracle_lib, prob, 60, 0.80, same_n_min=0.985)
+    _check_full(S, oracle_lib, prob, 60, chaotic=True)
 
 
 def test_torus_256_fp64_histories_follow_the_oracle(S, oracle_lib):

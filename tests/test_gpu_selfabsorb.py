@@ -7,7 +7,7 @@ import pytest
 from oracle import emission as E
 from oracle import selfabsorb as OSA
 from paper_1705_04702_gb300 import workloads as W
-from parity import CHAOTIC_CELL, MIXED_CELL_SIGNIFICANT, compare_tally
+from parity import K_SIGMA, REL_MIXED_TALLY, compare_tally
 from selfabsorb_case import PACKETS_PER_LAMBDA, SEED, stellar_case
 
 pytestmark = pytest.mark.gpu
@@ -73,24 +73,45 @@ def test_emission_totals(S, case):
 
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
 def test_cycles_match_oracle(S, case, precision):
+    """The whole loop against the oracle's loop.  The FP64 form follows it to
+    rounding.  In the mixed form a dust packet whose history diverges (the
+    clumpy torus amplifies FP32 rounding), or whose cell is drawn from a CDF
+    shifted by an earlier cycle's differences, is a different Monte Carlo
+    sample: the differences are bounded by K_SIGMA standard deviations of the
+    difference of two independent runs, with the oracle's batch-means error
+    estimates (10 packet ranges per cycle), summed over the cycles that feed
+    a result; the last cycle's table also moves with its total emission."""
     import torch
     from paper_1705_04702_gb300.selfabsorb import self_absorption
     prob, A, mass, wl = case
     ref = OSA.self_absorption(prob.grid, A, prob.wl.lam, mass, PACKETS_PER_LAMBDA, SEED, tol=1e-2, max_cycles=12,
-                              wl=wl)
+                              wl=wl, batches=10)
     grid = S.Grid(prob.grid)
     out = self_absorption(grid, _dev(A, torch.float64), prob.wl.lam, _dev(mass, torch.float32), PACKETS_PER_LAMBDA,
                           SEED, tol=1e-2, max_cycles=12, precision=precision, wl=wl)
     grid.close()
     assert out["converged"] and out["cycles"] == ref["cycles"]
     fp64 = precision == 0
+    var_sum = 0.0
     for g, r in zip(out["history"], ref["history"]):
-        assert g["emitted"] == pytest.approx(r["emitted"], rel=1e-9 if fp64 else 2e-3)
-        assert g["absorbed"] == pytest.approx(r["absorbed"], rel=1e-6 if fp64 else 2e-3)
+        if fp64:
+            assert g["emitted"] == pytest.approx(r["emitted"], rel=1e-9)
+            assert g["absorbed"] == pytest.approx(r["absorbed"], rel=1e-6)
+        else:
+            # cycle k emits S + D_{k-1}: its difference is the previous cycles' absorbed differences
+            assert abs(g["emitted"] - r["emitted"]) <= K_SIGMA * np.sqrt(2 * var_sum) + 1e-9 * r["emitted"]
+            var_sum += r["var_absorbed"]
+            assert abs(g["absorbed"] - r["absorbed"]) <= K_SIGMA * np.sqrt(2 * var_sum) + REL_MIXED_TALLY * r["absorbed"]
         led = g["ledger"]
         closure = abs(led["emitted"] - led["absorbed"] - led["escaped"] - led["residual"]) / led["emitted"]
         assert closure < (1e-12 if fp64 else 1e-6)
-    # the last cycle's absorbed dust table, cell by cell (the clumpy torus
-    # amplifies rounding differences from event to event)
-    compare_tally(out["absorbed_dust"].cpu().numpy(), ref["absorbed_dust"], 1e-6 if fp64 else CHAOTIC_CELL,
-                  significant=1e-6 if fp64 else MIXED_CELL_SIGNIFICANT, l1=1e-6 if fp64 else 2e-3)
+    # the last cycle's absorbed dust table, cell by cell
+    gt = out["absorbed_dust"].cpu().numpy()
+    rt = ref["absorbed_dust"]
+    if fp64:
+        compare_tally(gt, rt, 1e-6, significant=1e-6, l1=1e-6)
+        return
+    shift = abs(out["history"][-1]["emitted"] - ref["history"][-1]["emitted"]) / ref["history"][-1]["emitted"]
+    bound = K_SIGMA * np.sqrt(2 * ref["var_absorbed_dust"]) + (2 * shift + REL_MIXED_TALLY) * np.abs(rt)
+    bad = np.abs(gt - rt) > bound + 1e-300
+    assert not bad.any(), (int(bad.sum()), np.abs(gt - rt)[bad][:5], bound[bad][:5])

@@ -99,6 +99,34 @@ def test_band_features():
     np.testing.assert_allclose(tot, a.sum(axis=1), rtol=1e-14)
 
 
+def test_band_features_floor_of_empty_bands():
+    """Cells with empty bands, computed by hand: an empty band sits at
+    1e-6 of the cell's total absorbed power shared over the 32 bands, per unit
+    mass; a dust-free or unheated cell sits at 1e-30 in every band.
+    Cell 0: power 2 at the first wavelength only, mass 0.5:
+      band 0 = log10(2 / 0.5) = log10(4); the rest log10(1e-6 * 2 / 32 / 0.5) = log10(1.25e-7).
+    Cell 1: power 3 at the first and 1 at the last wavelength, mass 2:
+      band 0 = log10(1.5), band 31 = log10(0.5), the rest log10(1e-6 * 4 / 32 / 2) = log10(6.25e-8).
+    Cell 2: no dust; cell 3: no absorbed power."""
+    lam_in = np.geomspace(0.1, 10.0, 50)
+    a = np.zeros((4, 50))
+    a[0, 0] = 2.0
+    a[1, 0] = 3.0
+    a[1, -1] = 1.0
+    a[2, 5] = 1.0
+    m = np.array([0.5, 2.0, 0.0, 1.0])
+    B, x, tot = E.band_features(a, lam_in, m)
+    exp = np.empty((4, E.NBANDS))
+    exp[0] = math.log10(1.25e-7)
+    exp[0, 0] = math.log10(4.0)
+    exp[1] = math.log10(6.25e-8)
+    exp[1, 0] = math.log10(1.5)
+    exp[1, 31] = math.log10(0.5)
+    exp[2:] = -30.0
+    np.testing.assert_allclose(x, exp, rtol=1e-14, atol=1e-14)
+    np.testing.assert_array_equal(tot, [2.0, 4.0, 1.0, 0.0])
+
+
 def _params(rng, scale=0.3):
     return {"W1": rng.normal(size=(128, 32)) * scale, "b1": rng.normal(size=128) * 0.1,
             "W2": rng.normal(size=(128, 128)) * scale / 3, "b2": rng.normal(size=128) * 0.1,
