@@ -415,7 +415,14 @@ def trace_rooflines(led, packets, k_ms, ninstr, red_rate, peak, peak_kind, kerne
             "frac": reds / t / red_rate, "traffic": hbm["traffic"], "kernel": kernel, "kernel_ms": k_ms,
             "atomics_per_packet": reds / packets,
             "peak_source": "measured in this run: random red.global.add.f64 into a table of the absorbed table's size"}
-    binding = dict(atom if atom["frac"] >= hbm["frac"] else hbm)
+    if atom["frac"] > 1.0:
+        # the deposits of a traversal share sectors (consecutive cells along x;
+        # wavelength-major tables), which the random-address microbenchmark
+        # does not: its rate is then no bound for this kernel
+        atom["note"] = "not a bound for this access stream (fraction > 1: deposits share sectors)"
+        binding = dict(hbm)
+    else:
+        binding = dict(atom if atom["frac"] >= hbm["frac"] else hbm)
     binding["min_of"] = {"hbm_frac": hbm["frac"], "atomics_frac": atom["frac"]}
     out = {"roofline": binding, "roofline_hbm": hbm, "roofline_atomic": atom}
     if ISSUE_INST_PER_PACKET and clock_mhz and sm_count:

@@ -611,6 +611,10 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
         put(ints, sizeof ints);
         put(&A, sizeof A);
         put(&s, sizeof s);
+        // output pointers the recorded work writes outside A: the transpose's
+        // destination (the caller's table, or its staging area) and the SEDs
+        put(&d_abs, sizeof d_abs);
+        put(&d_img, sizeof d_img);
         put(&d_sed, sizeof d_sed);
         put(npk, sizeof(uint64_t) * NL);
         put(P.npx.data(), sizeof(int) * ninstr);

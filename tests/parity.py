@@ -14,7 +14,7 @@ tolerances"):
   MIXED_CELL_SIGNIFICANT of the total within 1e-4.  Below that share a
   cell's tally is made of too few crossings to average the FP32 segment
   errors (absolute ~ t 2^-23 per crossing, t the distance from the
-  traversal's start): see cell_error_share().
+  traversal's start).
 * Images: pixel indices are decided by FP32 positions, so a peel-off within
   ~|x| 2^-21 of a pixel border can land in the neighbouring pixel.  Images
   are compared element by element after summing b x b pixel blocks, with b
@@ -147,23 +147,30 @@ def compare_images(gpu_images, ref_images, prob, rel, significant):
         compare_tally(rebin(gpu_images[q], b), rebin(ref_images[q], b), rel, significant=significant)
 
 
-def cell_error_share(prob):
-    """Share of the total below which a mixed-form cell tally is not checked
-    element by element.  A crossing's FP32 segment length carries an absolute
-    error up to ~t 2^-23 (t <= the grid diagonal D); its deposit error is
-    that times the local extinction.  A cell's relative error is therefore
-    about D 2^-23 / s over the mean length s of the segments that fill it,
-    which is below 1e-4 once a few segments of typical length (a fraction of
-    the cell size h) add up, but not for a cell lit by one short corner
-    segment.  Cells that hold a share of the absorbed luminosity of at least
-    MIXED_CELL_SIGNIFICANT collect many crossings at the packet counts of
-    the tests (>= 1000 packets), so that share is the threshold; the
-    function returns the ratio D 2^-23 / h that the threshold relies on being
-    << 1e-4 * (crossings per significant cell)."""
-    x0, x1, y0, y1, z0, z1 = prob.grid.bbox
-    D = float(np.sqrt((x1 - x0) ** 2 + (y1 - y0) ** 2 + (z1 - z0) ** 2))
-    h = min((x1 - x0) / prob.grid.nx, (y1 - y0) / prob.grid.ny, (z1 - z0) / prob.grid.nz)
-    return D * 2.0 ** -23 / h
+U_MAX = 1e-3  # largest share of unmatched packets the smooth-media record criterion allows
+
+
+def compare_tally_mc(gpu, ref, var, rel, significant, u=U_MAX, k=K_SIGMA):
+    """Tallies of many packets where the unmatched packets (a share u of all,
+    at most U_MAX in smooth media) cannot be split off one by one: each entry
+    holding >= significant of the total must agree within rel of its value
+    plus k standard deviations of the difference that u of the packets make
+    as independent samples, sqrt(2 u var) (var: the Monte Carlo variance of
+    the entry's total, e.g. batch means); the L1-normalised difference within
+    rel plus the same allowance summed.  Returns the L1 difference."""
+    gpu = np.asarray(gpu, np.float64).ravel()
+    ref = np.asarray(ref, np.float64).ravel()
+    var = np.asarray(var, np.float64).ravel()
+    tot = np.abs(ref).sum()
+    allow = k * np.sqrt(2.0 * u * var)
+    big = np.abs(ref) >= significant * tot
+    d = np.abs(gpu - ref)
+    bad = big & (d > rel * np.abs(ref) + allow)
+    assert not bad.any(), ("entries beyond rel + k sigma", int(bad.sum()), (d / np.abs(ref))[bad][:5],
+                           (allow / np.abs(ref))[bad][:5])
+    l1 = d.sum() / tot
+    assert l1 <= rel + allow.sum() / tot, (l1, allow.sum() / tot)
+    return float(l1)
 
 
 def unmatched(gpu, ref, prob, rel):
@@ -237,6 +244,30 @@ def packet_tallies_gpu(S, grid, prob, pairs, bins, template, precision, **run_kw
         _add(acc, parts, 1)
         _add(sq, parts, 2)
     return acc, sq
+
+
+def split_check(gpu_tot, ref_tot, gpu_f, ref_f, gpu_f2, ref_f2, rel, significant, k=K_SIGMA):
+    """gpu_tot / ref_tot: tallies of all packets; gpu_f / ref_f: the sums of
+    the unmatched packets' own tallies, gpu_f2 / ref_f2 their sums of
+    squares.  The matched packets' part (total minus unmatched) must agree
+    within rel (entries >= significant of the total, and L1); the unmatched
+    part must differ by at most k standard deviations of the difference of two
+    independent samples of those packets, sqrt(gpu_f2 + ref_f2), entry by
+    entry and summed over all entries.  Returns (matched part's L1, unmatched
+    part's L1 share of the total)."""
+    g = np.asarray(gpu_tot, np.float64).ravel()
+    r = np.asarray(ref_tot, np.float64).ravel()
+    gf = np.asarray(gpu_f, np.float64).ravel()
+    rf = np.asarray(ref_f, np.float64).ravel()
+    var = np.asarray(gpu_f2, np.float64).ravel() + np.asarray(ref_f2, np.float64).ravel()
+    # the subtraction leaves FP64 rounding of the totals, far below rel
+    l1 = compare_tally(g - gf, r - rf, rel, significant=significant)
+    d = gf - rf
+    sig = np.sqrt(var)
+    bad = np.abs(d) > k * sig + 1e-12 * np.abs(r)
+    assert not bad.any(), ("unmatched packets beyond k sigma", int(bad.sum()), d[bad][:5], sig[bad][:5])
+    assert abs(d.sum()) <= k * np.sqrt(var.sum()) + 1e-12 * abs(r.sum()), (d.sum(), np.sqrt(var.sum()))
+    return l1, float(np.abs(d).sum() / max(np.abs(r).sum(), 1e-300))
 
 
 def check_mixed(S, oracle_lib, grid, prob, g, r, chaotic=False, min_match=0.999,

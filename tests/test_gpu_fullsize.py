@@ -10,8 +10,8 @@ import pytest
 
 from paper_1705_04702_gb300 import workloads as W
 
-from parity import (REL_MIXED_PACKET, REL_MIXED_TALLY, compare_records, compare_tally, rebin, rebin_factor,
-                    record_sigma_check, scattering_counts_agree, unmatched)
+from parity import (REL_MIXED_PACKET, REL_MIXED_TALLY, compare_records, compare_tally, compare_tally_mc, rebin,
+                    rebin_factor, record_sigma_check, scattering_counts_agree, unmatched)
 
 pytestmark = pytest.mark.gpu
 
@@ -60,17 +60,20 @@ def test_disk_1e8_packets_sampled(S, oracle_lib):
 def test_disk_1e7_packets_full_grid(S):
     """The bench's workload and launch configuration (mixed form, persistent
     launch from a CUDA graph) at 1e7 packets against the oracle run over the
-    same packets on every host core: every absorbed cell and every rebinned
-    pixel block holding >= 1e-4 of its table's total within 1e-4, the
-    L1-normalised differences within 1e-4, SEDs and ledger within 1e-4."""
+    same packets on every host core.  The first 1e5 packets: >= 99.9% match
+    (same scatterings, every record field within 1e-5).  Tables: every
+    absorbed cell and every rebinned pixel block holding >= 1e-4 of its
+    table's total within 1e-4 plus the Monte Carlo allowance of the <= 0.1%
+    unmatched packets (parity.compare_tally_mc, with the batch-means variance
+    over the oracle workers' packet ranges); SEDs and ledger within 1e-4."""
     from oracle_pool import trace_all_cores
     n = 10_000_000
+    nrec = 100_000
     spec = {"maker": "disk_problem", "kwargs": {"npackets": n, "n": 256, "nlambda": 1, "npx": 512}}
-    ref = trace_all_cores(spec, n)
+    ref = trace_all_cores(spec, n, nrec=nrec)
     prob = W.disk_problem(n, n=256, nlambda=1, npx=512)
-    g = S.run_problem(prob, precision=S.PREC_MIXED, schedule=S.SCHED_PERSISTENT, use_graph=True)
+    g = S.run_problem(prob, precision=S.PREC_MIXED, schedule=S.SCHED_PERSISTENT, use_graph=True, nrec=nrec)
     assert g["status"] == S.OK and ref["status"] == 0
-    ga = g["absorbed"].cpu().numpy()
     report = {"oracle_cores": ref["cores"]}
     fails = []
 
@@ -80,17 +83,23 @@ def test_disk_1e7_packets_full_grid(S):
         except AssertionError as e:
             fails.append((name, str(e)[:300]))
 
-    check("absorbed_l1", lambda: compare_tally(ga, ref["absorbed"], REL_MIXED_TALLY, significant=1e-4))
+    small = prob.with_packets(nrec)
+    check("records", lambda: compare_records(g["records"].cpu().numpy(), ref["records"], small, REL_MIXED_PACKET,
+                                             0.999, same_n_min=0.999))
+    check("absorbed", lambda: compare_tally_mc(g["absorbed"].cpu().numpy(), ref["absorbed"], ref["absorbed_var"],
+                                               REL_MIXED_TALLY, 1e-4))
     off = 0
+    B = float(ref["cores"])
     for q, ins in enumerate(prob.instruments):
         k = ins.npx * ins.npx
-        gi = g["images"][q].cpu().numpy()
-        ri = ref["images"][off:off + k].reshape(ins.npx, ins.npx, 1)
-        off += k
         b = rebin_factor(prob, ins)
+        gi = rebin(g["images"][q].cpu().numpy(), b)
+        ri = rebin(ref["images"][off:off + k].reshape(ins.npx, ins.npx, 1), b)
+        parts = [rebin(p[off:off + k].reshape(ins.npx, ins.npx, 1), b) for p in ref["images_parts"]]
+        var = B / (B - 1.0) * sum((p - ri / B) ** 2 for p in parts)
+        off += k
         report[f"image{q}_bin"] = b
-        check(f"image{q}_l1", lambda gi=gi, ri=ri, b=b: compare_tally(rebin(gi, b), rebin(ri, b), REL_MIXED_TALLY,
-                                                                        significant=1e-4))
+        check(f"image{q}", lambda gi=gi, ri=ri, var=var: compare_tally_mc(gi, ri, var, REL_MIXED_TALLY, 1e-4))
     check("sed", lambda: compare_tally(g["sed"].cpu().numpy(), ref["sed"], REL_MIXED_TALLY, significant=0.0))
     check("ledger", lambda: np.testing.assert_allclose(g["ledger_per_lambda"], ref["ledger"], rtol=REL_MIXED_TALLY))
     print(report, fails)

@@ -1,6 +1,8 @@
 """GPU parity of the dust self-absorption cycles (Sect. 3.2): the exact
 emission from two absorbed tables, the emission totals, and the whole cycle
 loop, against the FP64 oracle on the same inputs and Philox streams."""
+import math
+
 import numpy as np
 import pytest
 
@@ -112,6 +114,10 @@ def test_cycles_match_oracle(S, case, precision):
         compare_tally(gt, rt, 1e-6, significant=1e-6, l1=1e-6)
         return
     shift = abs(out["history"][-1]["emitted"] - ref["history"][-1]["emitted"]) / ref["history"][-1]["emitted"]
-    bound = K_SIGMA * np.sqrt(2 * ref["var_absorbed_dust"]) + (2 * shift + REL_MIXED_TALLY) * np.abs(rt)
+    # the mixed form ends a deposit traversal once its optical depth passes 30
+    # and drops deposits below the FP32 range: at most e^-30 of the cycle's
+    # emitted luminosity goes missing from any cell
+    cut = math.exp(-30.0) * ref["history"][-1]["emitted"]
+    bound = K_SIGMA * np.sqrt(2 * ref["var_absorbed_dust"]) + (2 * shift + REL_MIXED_TALLY) * np.abs(rt) + cut
     bad = np.abs(gt - rt) > bound + 1e-300
     assert not bad.any(), (int(bad.sum()), np.abs(gt - rt)[bad][:5], bound[bad][:5])
