@@ -308,9 +308,10 @@ int skirt_band_features(const double* absorbed, long long ncell, int n_in, const
 
 /* The MLP surrogate 32 -> 128 -> 128 -> 100 (SiLU, SiLU, softmax): input
  * the 32 band features standardised with the training set's mean / std,
- * output the normalised emission shape, times total(m).  Inference runs on
- * the tensor cores with BF16 weights and activations, FP32 accumulation;
- * training keeps FP32 master weights.  The network also stores the
+ * output the normalised emission shape, times total(m).  Inference and
+ * training run on the tensor cores with BF16 operands and FP32 accumulation;
+ * training keeps FP32 master weights (and FP32 SiLU derivatives, softmax and
+ * bias sums).  The network also stores the
  * per-feature range [lo, hi] of its training inputs (the "hull"). */
 typedef struct skirt_mlp_s* skirt_mlp_t;
 int skirt_mlp_create(skirt_mlp_t* out, uint64_t seed); /* Kaiming-uniform init from seed */
@@ -339,9 +340,13 @@ int skirt_mlp_train_opts_default(skirt_mlp_train_opts* opts);
 int skirt_mlp_train(skirt_mlp_t net, const float* features, const double* emission, long long n,
                     const skirt_mlp_train_opts* opts, float* loss_history, void* stream);
 
-/* One batch of the training arithmetic (FP32): loss and gradient of the
- * mean cross-entropy with respect to the packed FP32 parameters, for the
- * standardised inputs x_std (device float[n][32]) -> grad: host float[SKIRT_MLP_NPARAM]. */
+/* One batch of the training arithmetic: loss and gradient of the mean
+ * cross-entropy with respect to the packed FP32 parameters, for the
+ * standardised inputs x_std (device-or-host float[n][32]) and target shapes
+ * (device-or-host float[n][100]) -> grad: host float[SKIRT_MLP_NPARAM].
+ * Every operand of a product is rounded to BF16 (inputs, weights,
+ * activations, back-propagated dz); accumulation, SiLU derivatives, softmax
+ * and the bias sums are FP32. */
 int skirt_mlp_grad(skirt_mlp_t net, const float* x_std, const float* target, int n, float* grad, float* loss,
                    void* stream);
 

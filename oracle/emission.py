@@ -237,24 +237,36 @@ def mlp_loss(params, x_std, target):
     return float(-np.sum(target * np.log(np.maximum(p, 1e-300))) / x_std.shape[0])
 
 
-def mlp_grad(params, x_std, target):
+def mlp_grad(params, x_std, target, bf16=False):
     """Gradients of mlp_loss by reverse-mode differentiation written out
-    layer by layer (softmax + cross-entropy: dL/dz3 = (p - t) / n)."""
+    layer by layer (softmax + cross-entropy: dL/dz3 = (p - t) / n), and the
+    loss.  With bf16, every operand of a matrix product is rounded to
+    bfloat16 first, as the tensor-core training kernel feeds its products:
+    the inputs, the weights, the activations and the back-propagated dz of
+    each layer (the bias gradients sum the unrounded dz).  Returns (grads,
+    mean loss)."""
     n = x_std.shape[0]
-    p, (a0, z1, a1, z2, a2, z3) = mlp_forward(params, x_std)
+    q = bf16_round if bf16 else (lambda v: np.asarray(v, dtype=np.float64))
+    W = {k: q(params[k]) if k.startswith("W") else np.asarray(params[k], np.float64) for k in params}
+    p, (a0, z1, a1, z2, a2, z3) = mlp_forward(W, x_std, act_bf16=bf16)
+    loss = float(-np.sum(target * np.log(np.maximum(p, 1e-300))) / n)
     d3 = (p - target) / n
-    g = {"W3": d3.T @ a2, "b3": d3.sum(axis=0)}
-    da2 = d3 @ params["W3"]
+    g = {"b3": d3.sum(axis=0)}
+    d3 = q(d3)
+    g["W3"] = d3.T @ a2
+    da2 = d3 @ W["W3"]
     s2 = 1.0 / (1.0 + np.exp(-z2))
     d2 = da2 * (s2 * (1.0 + z2 * (1.0 - s2)))
-    g["W2"] = d2.T @ a1
     g["b2"] = d2.sum(axis=0)
-    da1 = d2 @ params["W2"]
+    d2 = q(d2)
+    g["W2"] = d2.T @ a1
+    da1 = d2 @ W["W2"]
     s1 = 1.0 / (1.0 + np.exp(-z1))
     d1 = da1 * (s1 * (1.0 + z1 * (1.0 - s1)))
-    g["W1"] = d1.T @ a0
     g["b1"] = d1.sum(axis=0)
-    return g
+    d1 = q(d1)
+    g["W1"] = d1.T @ a0
+    return g, loss
 
 
 def surrogate_emission(params, x, total, mean, std, act_bf16=False):

@@ -11,9 +11,11 @@
 // written as FP64 emission.  The same pass flags rows whose raw features
 // leave the training hull.
 //
-// Training (skirt_mlp_train): FP32 master weights, tiled FP32 GEMMs,
-// explicit backward pass (softmax cross-entropy, SiLU'), Adam with cosine
-// step decay.
+// Training (skirt_mlp_train): FP32 master weights; every step is one fused
+// tensor-core kernel per 32 rows (forward, softmax cross-entropy, backward,
+// weight-gradient products; mlp_train.cu) and one kernel that sums the
+// partial gradients in order, takes the Adam step (cosine step decay) and
+// refreshes the BF16 weights.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -48,7 +50,6 @@ static_assert(OFF_B3 + NO == NPARAM, "packed parameter layout");
 // inference
 // --------------------------------------------------------------------------
 constexpr int INF_WARPS = 8;
-constexpr int SPLIT_MAX = 160;  // split-K slices of a weight-gradient product
 constexpr int INF_ROWS = 16 * INF_WARPS;
 // shared memory: W1 [128][32], W2 [128][128], W3 [104][128] (bf16) with
 // every row padded by 8 elements, so that the eight rows one fragment load
@@ -324,172 +325,8 @@ __global__ void __launch_bounds__(32 * INF_WARPS, 2) mlp_infer_kernel(
 }
 
 // --------------------------------------------------------------------------
-// training kernels (FP32)
+// training helpers (the step itself is in mlp_train.cu)
 // --------------------------------------------------------------------------
-// C[M][N] = op(A)[M][K] op(B)[K][N]; A is [M][K] (ta = 0) or [K][M] (ta = 1);
-// B is [K][N] (tb = 0) or [N][K] (tb = 1); all row-major.  64 x 64 tiles,
-// 256 threads, 4 x 4 outputs each.
-// With gridDim.z = S > 1 (split K), block z sums k in [z Kc, (z+1) Kc) and
-// writes its partial product to C + z M N; split_reduce_kernel adds the S
-// partials in order.
-__global__ void gemm_kernel(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ C, int M,
-                            int N, int K, int ta, int tb, int Kc)
-{
-    __shared__ float As[16][65], Bs[16][65];
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-    const int kb = blockIdx.z * Kc, ke = min(K, kb + Kc);
-    C += (size_t)blockIdx.z * M * N;
-    float acc[4][4] = {};
-    for (int k0 = kb; k0 < ke; k0 += 16) {
-        for (int i = threadIdx.x; i < 16 * 64; i += 256) {
-            const int kk = i / 64, mm = i % 64;
-            const int gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < M && gk < ke) ? (ta ? A[(size_t)gk * M + gm] : A[(size_t)gm * K + gk]) : 0.f;
-            const int gn = n0 + mm;
-            Bs[kk][mm] = (gn < N && gk < ke) ? (tb ? B[(size_t)gn * K + gk] : B[(size_t)gk * N + gn]) : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            float a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) { a[i] = As[kk][ty + 16 * i]; b[i] = Bs[kk][tx + 16 * i]; }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
-            if (gm < M && gn < N) C[(size_t)gm * N + gn] = acc[i][j];
-        }
-}
-
-// C[i] = sum over z < S of part[z][i], in order (deterministic split-K)
-__global__ void split_reduce_kernel(const float* __restrict__ part, float* __restrict__ C, int mn, int S)
-{
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < mn; i += gridDim.x * blockDim.x) {
-        float acc = 0.f;
-        for (int z = 0; z < S; ++z) acc += part[(size_t)z * mn + i];
-        C[i] = acc;
-    }
-}
-
-// z += bias (per column); a = silu(z)
-__global__ void bias_silu_kernel(float* z, float* a, const float* bias, int rows, int cols)
-{
-    const long long n = (long long)rows * cols;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float v = z[i] + bias[i % cols];
-        z[i] = v;
-        a[i] = v / (1.f + expf(-v));
-    }
-}
-
-// d = da * silu'(z)
-__global__ void silu_back_kernel(const float* z, const float* da, float* d, long long n)
-{
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float s = 1.f / (1.f + expf(-z[i]));
-        d[i] = da[i] * s * (1.f + z[i] * (1.f - s));
-    }
-}
-
-// per row: p = softmax(z + b3); loss += -sum t log p; dz = (p - t) / rows  (one warp per row)
-__global__ void softmax_xent_kernel(const float* z, const float* bias, const float* target, float* dz, int rows,
-                                    float* loss)
-{
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= rows) return;
-    const float* zr = z + (size_t)warp * NO;
-    const float* tr = target + (size_t)warp * NO;
-    float v[4], m = -3.0e38f;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int c = lane + 32 * k;
-        v[k] = c < NO ? zr[c] + bias[c] : -3.0e38f;
-        m = fmaxf(m, v[k]);
-    }
-    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    float s = 0.f;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) s += (lane + 32 * k < NO) ? expf(v[k] - m) : 0.f;
-    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    const float ls = logf(s);
-    float l = 0.f;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int c = lane + 32 * k;
-        if (c < NO) {
-            const float logp = v[k] - m - ls;
-            l -= tr[c] * logp;
-            dz[(size_t)warp * NO + c] = (expf(logp) - tr[c]) / (float)rows;
-        }
-    }
-    for (int o = 16; o; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-    if (lane == 0) atomicAdd(loss, l / (float)rows);
-}
-
-// out[c] = sum over rows of d[r][c]
-__global__ void colsum_kernel(const float* d, float* out, int rows, int cols)
-{
-    const int c = blockIdx.x;
-    float s = 0.f;
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) s += d[(size_t)r * cols + c];
-    __shared__ float red[256];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[c] = red[0];
-}
-
-// Adam with this step's learning rate and bias corrections read from the
-// schedule (sched[3t..3t+2] = lr, 1 - b1^(t+1), 1 - b2^(t+1)) at the device
-// step counter t, so that one captured graph serves every step
-__global__ void adam_sched_kernel(float* p, const float* g, float* m, float* v, int n, const float* __restrict__ sched,
-                                  const long long* __restrict__ t_dev, float b1, float b2, float eps)
-{
-    const long long t = *t_dev;
-    const float lr = sched[3 * t], c1 = sched[3 * t + 1], c2 = sched[3 * t + 2];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float gi = g[i];
-        const float mi = b1 * m[i] + (1.f - b1) * gi;
-        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-    }
-}
-
-// the batch of step t: sample r of the batch is (a (k B + r) + b) mod n with
-// k = t mod steps and (a, b) the permutation of epoch t / steps
-__global__ void gather_sched_kernel(const float* __restrict__ feat, const float* __restrict__ target, long long n,
-                                    const unsigned long long* __restrict__ ab, const long long* __restrict__ t_dev,
-                                    long long steps, int rows, const float* __restrict__ stats, float* __restrict__ xb,
-                                    float* __restrict__ tb)
-{
-    const long long t = *t_dev;
-    const unsigned long long a = ab[2 * (t / steps)], b = ab[2 * (t / steps) + 1];
-    const long long first = (t % steps) * rows;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < rows * (NIN + NO); i += gridDim.x * blockDim.x) {
-        const int r = i / (NIN + NO), c = i % (NIN + NO);
-        const unsigned long long src = (a * (unsigned long long)(first + r) + b) % (unsigned long long)n;
-        if (c < NIN) xb[(size_t)r * NIN + c] = (feat[src * NIN + c] - stats[c]) * stats[NIN + c];
-        else tb[(size_t)r * NO + (c - NIN)] = target[src * NO + (c - NIN)];
-    }
-}
-
-__global__ void step_advance_kernel(long long* t_dev) { *t_dev += 1; }
-
 // out[r][c] = in[r][c] / sum_c in[r][c] in FP32 (one warp per row; zero rows stay zero)
 __global__ void normalize_rows_kernel(const double* __restrict__ in, float* __restrict__ out, long long rows)
 {
@@ -756,32 +593,32 @@ extern "C" int skirt_mlp_train_opts_default(skirt_mlp_train_opts* o)
 
 namespace {
 
+// Per-call scratch of a training step: the per-CTA partial gradients and
+// losses, the loss accumulator and the reduction's block counter.
 struct Work {
-    float *xb = nullptr, *tb = nullptr, *z1 = nullptr, *a1 = nullptr, *z2 = nullptr, *a2 = nullptr, *z3 = nullptr,
-          *d3 = nullptr, *da = nullptr, *d = nullptr, *loss = nullptr;
-    float* part = nullptr;  // split-K partial products of the weight gradients
-    cudaError_t alloc(int B, cudaStream_t s)
+    float* part = nullptr;
+    float* part_loss = nullptr;
+    float* loss = nullptr;
+    unsigned* done = nullptr;
+    cudaError_t alloc(int rows, cudaStream_t s)
     {
+        const int ncta = (rows + train_rows_per_cta() - 1) / train_rows_per_cta();
         cudaError_t e;
-        if ((e = cudaMallocAsync((void**)&part, sizeof(float) * SPLIT_MAX * NH * NH, s))) return e;
-        if ((e = cudaMallocAsync((void**)&xb, sizeof(float) * B * NIN, s))) return e;
-        if ((e = cudaMallocAsync((void**)&tb, sizeof(float) * B * NO, s))) return e;
-        if ((e = cudaMallocAsync((void**)&z1, sizeof(float) * B * NH, s))) return e;
-        if ((e = cudaMallocAsync((void**)&a1, sizeof(float) * B * NH, s))) return e;
-        if ((e = cudaMallocAsync((void**)&z2, sizeof(float) * B * NH, s))) return e;
-        if ((e = cudaMallocAsync((void**)&a2, sizeof(float) * B * NH, s))) return e;
-        if ((e = cudaMallocAsync((void**)&z3, sizeof(float) * B * NO, s))) return e;
-        if ((e = cudaMallocAsync((void**)&d3, sizeof(float) * B * NO, s))) return e;
-        if ((e = cudaMallocAsync((void**)&da, sizeof(float) * B * NH, s))) return e;
-        if ((e = cudaMallocAsync((void**)&d, sizeof(float) * B * NH, s))) return e;
-        return cudaMallocAsync((void**)&loss, sizeof(float), s);
+        if ((e = cudaMallocAsync((void**)&part, sizeof(float) * (size_t)ncta * NPARAM, s))) return e;
+        if ((e = cudaMallocAsync((void**)&part_loss, sizeof(float) * (size_t)ncta, s))) return e;
+        if ((e = cudaMallocAsync((void**)&loss, sizeof(float), s))) return e;
+        if ((e = cudaMallocAsync((void**)&done, sizeof(unsigned), s))) return e;
+        if ((e = cudaMemsetAsync(loss, 0, sizeof(float), s))) return e;
+        return cudaMemsetAsync(done, 0, sizeof(unsigned), s);
     }
     void release(cudaStream_t s)
     {
-        for (float** p : {&xb, &tb, &z1, &a1, &z2, &a2, &z3, &d3, &da, &d, &loss, &part}) {
+        for (float** p : {&part, &part_loss, &loss}) {
             if (*p) cudaFreeAsync(*p, s);
             *p = nullptr;
         }
+        if (done) cudaFreeAsync(done, s);
+        done = nullptr;
     }
 };
 
@@ -792,6 +629,8 @@ struct TrainScope {
     cudaStream_t s = nullptr;
     Work w;
     float* target = nullptr;
+    float* x_in = nullptr;    // the gradient call's copies of its rows
+    float* t_in = nullptr;
     double* d_st = nullptr;
     unsigned long long* d_ab = nullptr;
     float* d_sched = nullptr;
@@ -813,6 +652,8 @@ struct TrainScope {
         if (ready) cudaEventDestroy(ready);
         w.release(s);
         if (target) cudaFreeAsync(target, s);
+        if (x_in) cudaFreeAsync(x_in, s);
+        if (t_in) cudaFreeAsync(t_in, s);
         if (d_st) cudaFreeAsync(d_st, s);
         if (d_ab) cudaFreeAsync(d_ab, s);
         if (d_sched) cudaFreeAsync(d_sched, s);
@@ -820,54 +661,6 @@ struct TrainScope {
         cudaGetLastError();
     }
 };
-
-void gemm(const float* A, const float* B, float* C, int M, int N, int K, int ta, int tb, cudaStream_t s)
-{
-    dim3 grid((N + 63) / 64, (M + 63) / 64);
-    gemm_kernel<<<grid, 256, 0, s>>>(A, B, C, M, N, K, ta, tb, K);
-}
-
-// weight gradient C[M][N] = A^T B over the batch (K = batch rows): few output
-// tiles and a long K, so K is split across blocks (at least ~2 blocks per SM)
-// with a deterministic reduction of the partials
-void gemm_wgrad(const float* A, const float* B, float* C, int M, int N, int K, float* part, cudaStream_t s)
-{
-    const int tiles = ((N + 63) / 64) * ((M + 63) / 64);
-    int S = (304 + tiles - 1) / tiles;
-    if (S > SPLIT_MAX) S = SPLIT_MAX;
-    int Kc = (K + S - 1) / S;
-    Kc = (Kc + 15) & ~15;
-    S = (K + Kc - 1) / Kc;
-    dim3 grid((N + 63) / 64, (M + 63) / 64, S);
-    gemm_kernel<<<grid, 256, 0, s>>>(A, B, part, M, N, K, 1, 0, Kc);
-    split_reduce_kernel<<<(M * N + 255) / 256, 256, 0, s>>>(part, C, M * N, S);
-}
-
-// forward + backward of one batch already in w.xb / w.tb; gradient into net->G, loss added to *w.loss
-void fwd_bwd(skirt_mlp_s* net, Work& w, int B, cudaStream_t s)
-{
-    const float* P = net->P;
-    float* G = net->G;
-    gemm(w.xb, P + OFF_W1, w.z1, B, NH, NIN, 0, 1, s);
-    bias_silu_kernel<<<blocks_for((long long)B * NH, 256), 256, 0, s>>>(w.z1, w.a1, P + OFF_B1, B, NH);
-    gemm(w.a1, P + OFF_W2, w.z2, B, NH, NH, 0, 1, s);
-    bias_silu_kernel<<<blocks_for((long long)B * NH, 256), 256, 0, s>>>(w.z2, w.a2, P + OFF_B2, B, NH);
-    gemm(w.a2, P + OFF_W3, w.z3, B, NO, NH, 0, 1, s);
-    softmax_xent_kernel<<<(B * 32 + 255) / 256, 256, 0, s>>>(w.z3, P + OFF_B3, w.tb, w.d3, B, w.loss);
-    // layer 3
-    gemm_wgrad(w.d3, w.a2, G + OFF_W3, NO, NH, B, w.part, s);
-    colsum_kernel<<<NO, 256, 0, s>>>(w.d3, G + OFF_B3, B, NO);
-    gemm(w.d3, P + OFF_W3, w.da, B, NH, NO, 0, 0, s);
-    silu_back_kernel<<<blocks_for((long long)B * NH, 256), 256, 0, s>>>(w.z2, w.da, w.d, (long long)B * NH);
-    // layer 2
-    gemm_wgrad(w.d, w.a1, G + OFF_W2, NH, NH, B, w.part, s);
-    colsum_kernel<<<NH, 256, 0, s>>>(w.d, G + OFF_B2, B, NH);
-    gemm(w.d, P + OFF_W2, w.da, B, NH, NH, 0, 0, s);
-    silu_back_kernel<<<blocks_for((long long)B * NH, 256), 256, 0, s>>>(w.z1, w.da, w.d, (long long)B * NH);
-    // layer 1
-    gemm_wgrad(w.d, w.xb, G + OFF_W1, NH, NIN, B, w.part, s);
-    colsum_kernel<<<NH, 256, 0, s>>>(w.d, G + OFF_B1, B, NH);
-}
 
 }  // namespace
 
@@ -879,11 +672,15 @@ extern "C" int skirt_mlp_grad(skirt_mlp_t net, const float* x_std, const float* 
     TrainScope sc(s);
     Work& w = sc.w;
     MCK(w.alloc(n, s));
-    MCK(cudaMemcpyAsync(w.xb, x_std, sizeof(float) * n * NIN, cudaMemcpyDefault, s));
-    MCK(cudaMemcpyAsync(w.tb, target, sizeof(float) * n * NO, cudaMemcpyDefault, s));
-    MCK(cudaMemsetAsync(w.loss, 0, sizeof(float), s));
-    fwd_bwd(net, w, n, s);
-    MCK(cudaGetLastError());
+    float*& d_x = sc.x_in;
+    float*& d_t = sc.t_in;
+    MCK(cudaMallocAsync((void**)&d_x, sizeof(float) * (size_t)n * NIN, s));
+    MCK(cudaMallocAsync((void**)&d_t, sizeof(float) * (size_t)n * NO, s));
+    MCK(cudaMemcpyAsync(d_x, x_std, sizeof(float) * (size_t)n * NIN, cudaMemcpyDefault, s));
+    MCK(cudaMemcpyAsync(d_t, target, sizeof(float) * (size_t)n * NO, cudaMemcpyDefault, s));
+    if (int r = repack(net, s)) return r;
+    MCK(launch_train_step(net->Wb, net->P, nullptr, d_t, nullptr, nullptr, nullptr, 0, n, d_x, n, w.part, w.part_loss,
+                          net->G, 0, nullptr, nullptr, nullptr, nullptr, 0.f, 0.f, 0.f, nullptr, w.loss, w.done, s));
     if (grad) MCK(cudaMemcpyAsync(grad, net->G, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost, s));
     float l = 0.f;
     MCK(cudaMemcpyAsync(&l, w.loss, sizeof(float), cudaMemcpyDeviceToHost, s));
@@ -961,8 +758,11 @@ extern "C" int skirt_mlp_train(skirt_mlp_t net, const float* features, const dou
     MCK(cudaMemcpyAsync(d_sched, sched.data(), sizeof(float) * sched.size(), cudaMemcpyHostToDevice, s));
     MCK(cudaMemsetAsync(d_t, 0, sizeof(long long), s));
 
-    // one training step (gather, forward, backward, Adam, step counter) as a
-    // CUDA graph, captured on a private stream and replayed for every step
+    // the BF16 weights the first step reads
+    if (int r = repack(net, s)) return r;
+    // one training step (the fused tensor-core tile kernel, then the ordered
+    // gradient sum with the Adam step and the step counter) as a CUDA graph,
+    // captured on a private stream and replayed for every step
     cudaStream_t& cs = sc.cs;
     MCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaEvent_t& ready = sc.ready;
@@ -974,13 +774,15 @@ extern "C" int skirt_mlp_train(skirt_mlp_t net, const float* features, const dou
     int rc = SKIRT_OK;
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        gather_sched_kernel<<<blocks_for((long long)B * (NIN + NO), 256), 256, 0, cs>>>(features, target, n, d_ab, d_t,
-                                                                                       steps, B, net->stats, w.xb,
-                                                                                       w.tb);
-        fwd_bwd(net, w, B, cs);
-        adam_sched_kernel<<<blocks_for(NPARAM, 256), 256, 0, cs>>>(net->P, net->G, net->Mo, net->Vo, NPARAM, d_sched,
-                                                                  d_t, opts->beta1, opts->beta2, opts->eps);
-        step_advance_kernel<<<1, 1, 0, cs>>>(d_t);
+        e = launch_train_step(net->Wb, net->P, features, target, net->stats, d_ab, d_t, steps, n, nullptr, B, w.part,
+                              w.part_loss, net->G, 1, net->P, net->Mo, net->Vo, d_sched, opts->beta1, opts->beta2,
+                              opts->eps, net->Wb, w.loss, w.done, cs);
+        if (e != cudaSuccess) {
+            cudaGraph_t broken = nullptr;
+            cudaStreamEndCapture(cs, &broken);
+            if (broken) cudaGraphDestroy(broken);
+            return set_error(SKIRT_ERR_CUDA, "training step launch: %s", cudaGetErrorString(e));
+        }
         e = cudaStreamEndCapture(cs, &graph);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);

@@ -183,6 +183,17 @@ struct PinnedBuf {
     }
 };
 
+// mlp_train.cu: one training step (adam = 1) or one gradient (adam = 0) of the
+// emission surrogate on nrows rows (see the kernels there)
+int train_rows_per_cta();
+size_t train_tile_smem_bytes();
+cudaError_t launch_train_step(const uint16_t* Wb, const float* P, const float* feat, const float* target,
+                              const float* stats, const unsigned long long* ab, long long* t_dev,
+                              long long steps, long long n_data, const float* x_std, int nrows, float* part,
+                              float* part_loss, float* G, int adam, float* Pw, float* Mo, float* Vo,
+                              const float* sched, float b1, float b2, float eps, uint16_t* Wb_out, float* loss_acc,
+                              unsigned* done, cudaStream_t s);
+
 // error reporting shared by the translation units (api.cu)
 int set_error(int code, const char* fmt, ...);
 

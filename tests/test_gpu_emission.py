@@ -87,12 +87,21 @@ def test_training_gradient_matches_oracle(S):
     t = rng.random((n, 100))
     t = (t / t.sum(axis=1, keepdims=True)).astype(np.float32)
     g, loss = net.grad(_dev(x, torch.float32), _dev(t, torch.float32), n)
-    ref = E.mlp_grad(P32, x.astype(np.float64), t.astype(np.float64))
-    assert loss == pytest.approx(E.mlp_loss(P32, x.astype(np.float64), t.astype(np.float64)), rel=1e-5)
+    # the oracle with the kernel's BF16 rounding points; what remains is FP32
+    # against FP64 accumulation, and the rare BF16 rounding that an FP32 value
+    # on the other side of a rounding boundary takes (one BF16 unit, 2^-8, of
+    # one element of one operand)
+    ref, ref_loss = E.mlp_grad(P32, x.astype(np.float64), t.astype(np.float64), bf16=True)
+    assert loss == pytest.approx(ref_loss, rel=1e-5)
     gd = S.unpack_params(g)
     for k in ref:
         scale = np.abs(ref[k]).max()
-        np.testing.assert_allclose(gd[k], ref[k], rtol=0, atol=2e-4 * scale, err_msg=k)
+        np.testing.assert_allclose(gd[k], ref[k], rtol=0, atol=2e-3 * scale, err_msg=k)
+    # and the exact gradient within the BF16 rounding bound of the oracle pin
+    exact, _ = E.mlp_grad(P32, x.astype(np.float64), t.astype(np.float64))
+    for k in exact:
+        scale = np.abs(exact[k]).max()
+        assert np.abs(gd[k] - exact[k]).max() <= 16 * 2.0 ** -9 * scale, k
     net.close()
 
 

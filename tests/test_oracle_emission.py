@@ -139,7 +139,8 @@ def test_mlp_gradient_matches_finite_differences():
     x = rng.normal(size=(6, 32))
     t = rng.random((6, 100))
     t /= t.sum(axis=1, keepdims=True)
-    g = E.mlp_grad(P, x, t)
+    g, loss = E.mlp_grad(P, x, t)
+    assert loss == pytest.approx(E.mlp_loss(P, x, t), rel=1e-14)
     # central differences: truncation ~h^2, roundoff ~eps L / h ~ 1e-10 at h = 1e-5
     h = 1e-5
     for name, picks in (("W1", [(0, 0), (5, 31), (127, 7)]), ("b1", [(3,), (120,)]),
@@ -152,6 +153,28 @@ def test_mlp_gradient_matches_finite_differences():
             Pm[name][ij] -= h
             fd = (E.mlp_loss(Pp, x, t) - E.mlp_loss(Pm, x, t)) / (2 * h)
             assert g[name][ij] == pytest.approx(fd, rel=1e-5, abs=1e-9), (name, ij)
+
+
+def test_mlp_gradient_with_bfloat16_operands():
+    """The BF16-operand gradient (the tensor-core training arithmetic) stays
+    within the rounding bound of the exact one, which the finite differences
+    above pin: every product sees operands with relative errors <= 2^-9, and
+    a gradient entry collects them from at most six rounding stages (input,
+    two activations, three weights, three dz) along its path, so it moves by
+    well under 16 x 2^-9 of its tensor's scale; and the rounding is applied
+    (the two differ)."""
+    rng = np.random.default_rng(8)
+    P = _params(rng)
+    x = rng.normal(size=(64, 32))
+    t = rng.random((64, 100))
+    t /= t.sum(axis=1, keepdims=True)
+    g, _ = E.mlp_grad(P, x, t)
+    gb, lb = E.mlp_grad(P, x, t, bf16=True)
+    for k in g:
+        scale = np.abs(g[k]).max()
+        assert np.abs(gb[k] - g[k]).max() <= 16 * 2.0 ** -9 * scale, k
+        assert np.abs(gb[k] - g[k]).max() > 0, k
+    assert lb == pytest.approx(E.mlp_loss(P, x, t), rel=16 * 2.0 ** -9)
 
 
 def test_surrogate_output_is_energy_exact():
