@@ -19,28 +19,6 @@ enum {
     ST_END_PACKET,
 };
 
-// Warp-aggregated FP64 reduction of at most one pending tally per lane: the
-// lane's target address in `addr` (nullptr: none) and its value in
-// wbuf[lane].  All 32 lanes of the warp call it together, so the full-warp
-// masks of the ballot and the match are exact.  Lanes with the same address
-// add their values through shared memory (in lane order) and the lowest of
-// them issues a single red.global.add.f64; every lane's addr is cleared.
-__device__ __forceinline__ void warp_tally_flush(double*& addr, double* wbuf)
-{
-    const unsigned pend = __ballot_sync(0xffffffffu, addr != nullptr);
-    if (!pend) return;
-    __syncwarp();
-    const unsigned peers = __match_any_sync(0xffffffffu, (unsigned long long)addr);
-    const int lane = threadIdx.x & 31;
-    if (addr && lane == __ffs(peers) - 1) {
-        double s = 0.0;
-        for (unsigned p = peers; p; p &= p - 1) s += wbuf[__ffs(p) - 1];
-        atomicAdd(addr, s);
-    }
-    addr = nullptr;
-    __syncwarp();
-}
-
 // Henyey-Greenstein phase function, normalised to average 1 over the sphere.
 template <typename R>
 __device__ __forceinline__ R hg_phase(R g, R mu)

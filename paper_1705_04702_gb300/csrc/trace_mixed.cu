@@ -143,10 +143,8 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
     extern __shared__ __align__(16) unsigned char smem[];
     InstrDev* sins = reinterpret_cast<InstrDev*>(smem);
     Cold& C = *reinterpret_cast<Cold*>(smem + align16(sizeof(InstrDev) * A.ninstr));
-    double* wbuf_all = reinterpret_cast<double*>(smem + align16(sizeof(InstrDev) * A.ninstr) + sizeof(Cold));
     for (int i = threadIdx.x; i < A.ninstr; i += blockDim.x) sins[i] = A.ins[i];
     const int t = threadIdx.x;
-    double* wbuf = wbuf_all + (t & ~31);
     C.l_emit[t] = C.l_abs[t] = C.l_esc[t] = C.l_res[t] = 0.0;
     C.q[t] = C.q_end[t] = 0;
     C.c_dep[t] = C.c_loc[t] = C.c_peel[t] = C.c_scat[t] = 0;
@@ -197,7 +195,6 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
     float k0 = 0.f, k1 = 0.f, k2 = 0.f;
     bool have_pc = false;
     int pc0 = 0, pc1 = 0, pc2 = 0;
-    double* tally = nullptr;  // pending peel-off tally (value in wbuf[lane]), flushed per warp
 
     auto axis_cell = [&](float xh, float xl, float lo, float d, int n, const float2* f) {
         int c = (int)fminf(fmaxf(floorf((xh - lo) / d), 0.f), (float)(n - 1));
@@ -671,21 +668,14 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                     const float fa = floorf((a + I.half_fov_f) * I.inv_dpx_f);
                     const float fb = floorf((b + I.half_fov_f) * I.inv_dpx_f);
                     if (flux >= 1.17549435e-38f) {
-                        // the pixel's tally (or the out-of-frame one) is added after the event
-                        // phase, where the whole warp aggregates its lanes' tallies
-                        double* addr;
+                        // one FP64 reduction per peel-off (lanes of a warp rarely share a
+                        // pixel; aggregating them measured no faster)
                         if (fa >= 0.f && fa < (float)I.npx && fb >= 0.f && fb < (float)I.npx) {
                             const long long pix = (long long)fb * I.npx + (long long)fa;
-                            addr = A.images + I.img_off + pix * NL + lam;
+                            atomicAdd(A.images + I.img_off + pix * NL + lam, f2d(flux));
                         } else {
-                            addr = A.oof + (size_t)pi * NL + lam;
+                            atomicAdd(A.oof + (size_t)pi * NL + lam, f2d(flux));
                         }
-                        // a lane tallies at most once per event phase (every tally ends a
-                        // peel-off traversal and the next step begins one); a second tally
-                        // would be added at once
-                        if (tally) atomicAdd(tally, wbuf[t & 31]);
-                        wbuf[t & 31] = f2d(flux);
-                        tally = addr;
                     }
                 }
                 C.peel_i[t] = pi + 1;
@@ -754,7 +744,6 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
             continue;
         }
         if (!stepping && alive) events();
-        warp_tally_flush(tally, wbuf);  // all 32 lanes reach this point together
     }
 
     flush_ledger();
@@ -769,7 +758,7 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
 size_t trace_mixed_smem_bytes(int ninstr, int block)
 {
     (void)block;
-    return align16(sizeof(InstrDev) * ninstr) + sizeof(Cold) + sizeof(double) * MAXB;
+    return align16(sizeof(InstrDev) * ninstr) + sizeof(Cold);
 }
 
 static cudaError_t set_smem_limit()

@@ -5,6 +5,7 @@ import math
 import numpy as np
 import pytest
 
+from paper_1705_04702_gb300 import tasks
 from paper_1705_04702_gb300 import workloads as W
 
 from parity import (MIXED_CELL_SIGNIFICANT, REL_FP64, REL_MIXED_PACKET, REL_MIXED_TALLY, check_mixed,
@@ -90,7 +91,7 @@ def test_packet_ranges_compose(S):
     nrec = int(prob.npk.max())
     for prec in (S.PREC_FP64, S.PREC_MIXED):
         full = S.run_problem(prob, grid, precision=prec, nrec=nrec)
-        cut = prob.npk // 3
+        _, cut = tasks.packet_share(prob.npk, 0, 3)
         a = S.run_problem(prob.with_packets(cut), grid, precision=prec, nrec=nrec, total_packets=prob.npk)
         b = S.run_problem(prob.with_packets(prob.npk - cut), grid, precision=prec, nrec=nrec, first_packet=cut,
                           total_packets=prob.npk)
