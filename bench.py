@@ -387,11 +387,11 @@ def run_selfabs_report(args):
 # the committed ncu capture of the kernel as it stands
 # (profiles/trace_mixed_kernel_disk256_3e6_full.md); None when the kernel has
 # changed since.
-ISSUE_INST_PER_PACKET = None
+ISSUE_INST_PER_PACKET = 23468.0
 # DRAM bytes (read + write) per packet of the trace kernel from one ncu
 # capture of a 3e6-packet launch of the kernel as it stands (profiles/),
 # scaled by the packets of the launch; None when the kernel has changed since.
-TRAFFIC_PER_PACKET = {"disk": None, "octree": None}
+TRAFFIC_PER_PACKET = {"disk": 30250.0, "octree": None}
 
 
 def trace_rooflines(led, packets, k_ms, ninstr, red_rate, peak, peak_kind, kernel, crossing_bytes, traffic_pp,
@@ -574,7 +574,9 @@ def main():
         tune = {"block": opts.block, "chunk": opts.chunk, "blocks_per_sm": opts.blocks_per_sm,
                 "step_min": opts.step_min, "autotuned": True, "candidates": rep["n"],
                 "sample_packets": rep["sample_packets"], "repeats": rep["repeats"],
+                "confirm_packets": rep["confirm_packets"],
                 "sample_ms_chosen": ch["ms"], "sample_ms_default": rep["points"][0]["ms"],
+                "confirm_ms_chosen": ch["ms_confirm"], "confirm_ms_default": rep["points"][0]["ms_confirm"],
                 "chosen_is_default": rep["chosen"] == 0}
 
     clocks = ClockSampler(local)

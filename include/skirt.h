@@ -243,21 +243,25 @@ int skirt_trace(skirt_grid_t grid, const skirt_source* src, const skirt_waveleng
  * 512 for the FP64 form) x refill chunks {1, 4, 16} x step_min {16, 20, 24}
  * (mixed form) x resident blocks per SM from the occupancy limit down,
  * halving.  After one untimed warm-up launch, every candidate is timed
- * `repeats` times (<= 0 selects 2) and scored by its fastest launch.  The
- * fastest candidate replaces the requested schedule only if it is faster by
- * more than 2%; the result is written into opts->block / chunk /
- * blocks_per_sm / step_min.  report (may be NULL) receives the sweep.  The
- * outputs are used as scratch and left zeroed.  Errors as skirt_trace. */
+ * `repeats` times (<= 0 selects 2) and scored by its fastest launch.  A
+ * small sample favours schedules that end a short run evenly, so the three
+ * fastest candidates and the requested schedule are timed again on a sample
+ * five times larger (at most the whole workload); the fastest of those
+ * replaces the requested schedule only if it is faster there by more than
+ * 2%.  The result is written into opts->block / chunk / blocks_per_sm /
+ * step_min.  report (may be NULL) receives the sweep.  The outputs are used
+ * as scratch and left zeroed.  Errors as skirt_trace. */
 enum { SKIRT_TUNE_MAX_POINTS = 256 };
 typedef struct {
     int block, chunk, blocks_per_sm, step_min;
     float ms;                /* fastest of the repeats, device time of the trace launch */
+    float ms_confirm;        /* time on the larger sample (0: not re-timed) */
 } skirt_tune_point;
 typedef struct {
     int n;                   /* candidates timed; point 0 is the requested schedule */
     int chosen;              /* index of the schedule written into opts */
     int repeats;
-    unsigned long long sample_packets;
+    unsigned long long sample_packets, confirm_packets;
     skirt_tune_point points[SKIRT_TUNE_MAX_POINTS];
 } skirt_tune_report;
 int skirt_autotune(skirt_grid_t grid, const skirt_source* src, const skirt_wavelengths* wl,
@@ -328,14 +332,26 @@ typedef struct {
     float lr;            /* Adam step size (default 2e-3, cosine-decayed to lr/20) */
     float beta1, beta2, eps; /* Adam moments (defaults 0.9, 0.999, 1e-8) */
     uint64_t seed;       /* batch order */
+    float guard_quantile; /* the guard's threshold: this quantile of the training rows' dominant-band
+                             share (default 0.99; >= 1 disables the guard) */
 } skirt_mlp_train_opts;
 int skirt_mlp_train_opts_default(skirt_mlp_train_opts* opts);
+
+/* The guard that sends rows to the exact solver besides the range hull: a
+ * row whose dominant band holds more than share_max of the cell's absorbed
+ * power (share = 1 / sum_b 10^(f_b - max_b f_b), from the raw features) is
+ * outside it.  Such cells are rare in training (their emission depends on
+ * where within the band the power sits, which the features do not say) and
+ * carry most of the surrogate's large errors.  share_max > 0; >= 1 disables
+ * it.  skirt_mlp_train sets it from the training rows (guard_quantile). */
+int skirt_mlp_set_guard(skirt_mlp_t net, float share_max);
+int skirt_mlp_get_guard(skirt_mlp_t net, float* share_max);
 
 /* Trains on n samples: features (device float[n][32], raw band features)
  * and emission (device double[n][100], e.g. the exact solver's output; every
  * row is normalised to sum 1 on the device and used as the target shape t)
- * with the cross-entropy loss -sum_l t_l log p_l.  Sets the standardisation
- * and the hull from the training features.  loss_history: host
+ * with the cross-entropy loss -sum_l t_l log p_l.  Sets the standardisation,
+ * the hull and the guard from the training features.  loss_history: host
  * float[epochs] (mean loss per epoch) or NULL. */
 int skirt_mlp_train(skirt_mlp_t net, const float* features, const double* emission, long long n,
                     const skirt_mlp_train_opts* opts, float* loss_history, void* stream);
@@ -354,7 +370,8 @@ int skirt_mlp_grad(skirt_mlp_t net, const float* x_std, const float* target, int
  * (features - mean) / std)) * total (device double[n]).  features: device
  * float[n][32], 16-byte aligned (its 128-byte rows are fetched by bulk
  * asynchronous copies).  If flags is not NULL (device unsigned char[n]) it
- * receives 1 for rows with total > 0 whose features fall outside the hull.
+ * receives 1 for rows with total > 0 whose features fall outside the hull or
+ * the guard (skirt_mlp_set_guard).
  * Errors: INVALID_ARG (also for unaligned features), CUDA. */
 int skirt_mlp_forward(skirt_mlp_t net, const float* features, const double* total, long long n,
                       double* emission, unsigned char* flags, void* stream);
@@ -368,7 +385,7 @@ typedef struct {
 /* Emission of every cell from its absorbed spectrum.  mode EXACT: the FP64
  * solver on every cell.  mode SURROGATE: band features -> MLP on every cell,
  * then the exact solver overwrites the rows whose features fall outside the
- * network's hull (net required).  absorbed: device double[ncell][n_in];
+ * network's hull or guard (net required).  absorbed: device double[ncell][n_in];
  * lambda_in: host double[n_in]; mass: device float[ncell]; emission: device
  * double[ncell][100]; temperature: device float[ncell][3] or NULL (exact rows
  * only; 0 for surrogate rows); stats: host or NULL. */

@@ -199,6 +199,14 @@ def band_features(absorbed, lam_in, mass, nbands=NBANDS):
     return B, x, absorbed.sum(axis=1)
 
 
+def dominant_share(x):
+    """Share of a row's absorbed power held by its dominant band, from the
+    band features x [n, 32] (log10 of band power per unit mass): the largest
+    band power over their sum."""
+    p = 10.0 ** (np.asarray(x, dtype=np.float64) - np.max(x, axis=1, keepdims=True))
+    return 1.0 / p.sum(axis=1)
+
+
 def bf16_round(a):
     """Round float values to bfloat16 (nearest, ties to even), returned as float64."""
     f = np.asarray(a, dtype=np.float32)

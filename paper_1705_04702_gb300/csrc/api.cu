@@ -3,6 +3,7 @@
 // once in a CUDA graph and replayed), SED finalisation and the energy ledger.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -701,13 +702,19 @@ extern "C" int skirt_autotune(skirt_grid_t g, const skirt_source* src, const ski
     if (wl->n < 1 || wl->n > 65536) return fail(SKIRT_ERR_INVALID_ARG, "wavelength count %d out of range", wl->n);
     if (repeats <= 0) repeats = 2;
     if (repeats > 16) return fail(SKIRT_ERR_INVALID_ARG, "repeats must be <= 16");
-    std::vector<uint64_t> sample(wl->n);
-    unsigned long long nsample = 0;
-    for (int j = 0; j < wl->n; ++j) {
-        uint64_t n = (uint64_t)std::llround((double)npk[j] * frac);
-        sample[j] = (npk[j] > 0 && n == 0) ? 1 : n;
-        nsample += sample[j];
-    }
+    auto make_sample = [&](double f, std::vector<uint64_t>& smp) {
+        unsigned long long tot = 0;
+        smp.assign(wl->n, 0);
+        for (int j = 0; j < wl->n; ++j) {
+            uint64_t n = (uint64_t)std::llround((double)npk[j] * f);
+            smp[j] = (npk[j] > 0 && n == 0) ? 1 : n;
+            tot += smp[j];
+        }
+        return tot;
+    };
+    std::vector<uint64_t> sample, confirm;
+    const unsigned long long nsample = make_sample(frac, sample);
+    const unsigned long long nconfirm = make_sample(std::min(1.0, 5.0 * frac), confirm);
     skirt_trace_opts o = *opts;
     o.schedule = SKIRT_SCHED_PERSISTENT;
     o.use_graph = 0;
@@ -749,32 +756,44 @@ extern "C" int skirt_autotune(skirt_grid_t g, const skirt_source* src, const ski
                     if (bps == 1) break;
                 }
     }
-    auto run = [&](const skirt_tune_point& p, float* ms) -> int {
+    auto run = [&](const skirt_tune_point& p, float* ms, const std::vector<uint64_t>& smp) -> int {
         o.block = p.block;
         o.chunk = p.chunk;
         o.blocks_per_sm = p.blocks_per_sm;
         o.step_min = p.step_min;
         skirt_ledger led;
-        int r = skirt_trace(g, src, wl, sample.data(), seed, ins, ninstr, &o, absorbed, images, sed, &led, nullptr,
+        int r = skirt_trace(g, src, wl, smp.data(), seed, ins, ninstr, &o, absorbed, images, sed, &led, nullptr,
                             stream);
         if (r && r != SKIRT_ERR_EVENT_CAP) return r;
         *ms = led.kernel_ms > 0 ? led.kernel_ms : 1e30f;
         return SKIRT_OK;
     };
     float warm = 0.f;
-    if (int r = run(cand[0], &warm)) return r;
+    if (int r = run(cand[0], &warm, sample)) return r;
     for (auto& p : cand) {
         p.ms = 1e30f;
+        p.ms_confirm = 0.f;
         for (int k = 0; k < repeats; ++k) {
             float ms = 0.f;
-            if (int r = run(p, &ms)) return r;
+            if (int r = run(p, &ms, sample)) return r;
             if (ms < p.ms) p.ms = ms;
         }
     }
+    // the three fastest and the requested schedule, again on the larger sample
+    std::vector<int> order(cand.size());
+    for (size_t i = 0; i < cand.size(); ++i) order[i] = (int)i;
+    std::sort(order.begin() + 1, order.end(), [&](int a, int b) { return cand[a].ms < cand[b].ms; });
+    const int nconf = std::min<int>(4, (int)cand.size());
+    if (int r = run(cand[0], &warm, confirm)) return r;  // warm-up at the larger size
+    for (int q = 0; q < nconf; ++q) {
+        float ms = 0.f;
+        if (int r = run(cand[order[q]], &ms, confirm)) return r;
+        cand[order[q]].ms_confirm = ms;
+    }
     int best = 0;
-    for (int i = 1; i < (int)cand.size(); ++i)
-        if (cand[i].ms < cand[best].ms) best = i;
-    const int chosen = cand[best].ms < 0.98f * cand[0].ms ? best : 0;
+    for (int q = 1; q < nconf; ++q)
+        if (cand[order[q]].ms_confirm < cand[best].ms_confirm) best = order[q];
+    const int chosen = cand[best].ms_confirm < 0.98f * cand[0].ms_confirm ? best : 0;
     opts->block = cand[chosen].block;
     opts->chunk = cand[chosen].chunk;
     opts->blocks_per_sm = cand[chosen].blocks_per_sm;
@@ -785,6 +804,7 @@ extern "C" int skirt_autotune(skirt_grid_t g, const skirt_source* src, const ski
         report->chosen = chosen;
         report->repeats = repeats;
         report->sample_packets = nsample;
+        report->confirm_packets = nconfirm;
         for (size_t i = 0; i < cand.size(); ++i) report->points[i] = cand[i];
     }
     // leave the outputs zeroed

@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -183,7 +184,7 @@ __device__ __forceinline__ void layer(const uint32_t (&a)[KT][4], const uint16_t
 __global__ void __launch_bounds__(32 * INF_WARPS, 2) mlp_infer_kernel(
     const uint16_t* __restrict__ Wg, const float* __restrict__ Bg, const float* __restrict__ stats,
     const float* __restrict__ features, const double* __restrict__ total, long long n,
-    double* __restrict__ emission, unsigned char* __restrict__ flags)
+    double* __restrict__ emission, unsigned char* __restrict__ flags, float inv_share_max)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     // stage the weights (bf16, contiguous W1 W2 W3) and biases / statistics
@@ -243,15 +244,29 @@ __global__ void __launch_bounds__(32 * INF_WARPS, 2) mlp_infer_kernel(
             if (lane == 0 && base + stride < n) mbar_wait(&bar[buf ^ 1], (unsigned)(((k + 1) >> 1) & 1));
             break;
         }
+        // the rows' absorbed powers for the epilogue, requested before the layers so that
+        // their latency overlaps with the products
+        const long long r0 = base + g, r1 = base + g + 8;
+        const double tot0 = r0 < n ? __ldcs(total + r0) : 0.0;
+        const double tot1 = r1 < n ? __ldcs(total + r1) : 0.0;
         const float* xs = xbuf + buf * 16 * NIN;  // [16][32]; rows past n hold stale values
-        // ---- hull check: row i, lane = feature; one ballot per row
+        // ---- guard: row i, lane = feature.  A row leaves the training hull when a
+        // feature leaves its range, or when its dominant band holds a larger share of
+        // the cell's absorbed power than the guard allows: sum_b 10^(f_b - f_max) is
+        // the inverse of that share.  One ballot per row.
         if (flags) {
             bool mine = false;
             const float lo_f = hlo[lane], hi_f = hhi[lane];
 #pragma unroll 4
             for (int i = 0; i < 16; ++i) {
                 const float v = xs[i * NIN + lane];
-                const unsigned out = __ballot_sync(0xffffffffu, !(v >= lo_f && v <= hi_f));
+                float m = v;
+#pragma unroll
+                for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                float e = exp2f((v - m) * 3.32192809f);
+#pragma unroll
+                for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+                const unsigned out = __ballot_sync(0xffffffffu, !(v >= lo_f && v <= hi_f) || e < inv_share_max);
                 if (lane == i) mine = out != 0;
             }
             const long long r = base + lane;
@@ -305,9 +320,8 @@ __global__ void __launch_bounds__(32 * INF_WARPS, 2) mlp_infer_kernel(
         s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
         // emission = shape x absorbed power, formed in FP32 (the shape is an FP32
         // softmax) and widened exactly to FP64
-        const long long r0 = base + g, r1 = base + g + 8;
-        const float f0 = r0 < n ? (float)total[r0] / s0 : 0.f;
-        const float f1 = r1 < n ? (float)total[r1] / s1 : 0.f;
+        const float f0 = r0 < n ? (float)tot0 / s0 : 0.f;
+        const float f1 = r1 < n ? (float)tot1 / s1 : 0.f;
 #pragma unroll
         for (int j = 0; j < NO_PAD / 8; ++j) {
             const int c = 8 * j + 2 * t;
@@ -338,6 +352,20 @@ __global__ void normalize_rows_kernel(const double* __restrict__ in, float* __re
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     const double inv = s > 0.0 ? 1.0 / s : 0.0;
     for (int c = lane; c < NO; c += 32) out[r * NO + c] = (float)(in[r * NO + c] * inv);
+}
+
+// share of a row's absorbed power in its dominant band, from its 32 band
+// features (log10 of the band powers per unit mass): 1 / sum_b 10^(f_b - f_max)
+__global__ void dominant_share_kernel(const float* __restrict__ feat, long long n, float* __restrict__ share)
+{
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
+        const float* f = feat + r * NIN;
+        float m = f[0];
+        for (int b = 1; b < NIN; ++b) m = fmaxf(m, f[b]);
+        float e = 0.f;
+        for (int b = 0; b < NIN; ++b) e += exp2f((f[b] - m) * 3.32192809f);
+        share[r] = 1.f / e;
+    }
 }
 
 // per-feature sums over n samples: sum, sum of squares, min, max (one block per feature)
@@ -427,6 +455,7 @@ struct skirt_mlp_s {
     float* Bb = nullptr;       // fp32 biases for inference (b3 padded)
     float* stats = nullptr;    // device: mean[32], 1/std[32], lo[32], hi[32]
     float host_stats[4 * NIN]; // mean, std, lo, hi
+    float share_max = 1.f;     // guard: rows whose dominant band holds more of the power go to the exact solver
     bool packed = false;
 };
 
@@ -473,8 +502,9 @@ int mlp_forward_internal(skirt_mlp_s* net, const float* features, const double* 
     long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
     if (grid > tiles) grid = tiles;
     if (grid < 1) grid = 1;
+    const float inv_share_max = net->share_max > 0.f ? 1.f / net->share_max : 3.0e38f;
     mlp_infer_kernel<<<(int)grid, 32 * INF_WARPS, SM_TOTAL, s>>>(net->Wb, net->Bb, net->stats, features, total, n,
-                                                                  emission, flags);
+                                                                  emission, flags, inv_share_max);
     MCK(cudaGetLastError());
     return SKIRT_OK;
 }
@@ -566,6 +596,21 @@ extern "C" int skirt_mlp_set_params(skirt_mlp_t net, const float* params, const 
     return upload_stats(net);
 }
 
+extern "C" int skirt_mlp_set_guard(skirt_mlp_t net, float share_max)
+{
+    if (!net) return set_error(SKIRT_ERR_INVALID_ARG, "net is NULL");
+    if (!(share_max > 0.f)) return set_error(SKIRT_ERR_INVALID_ARG, "share_max must be > 0");
+    net->share_max = share_max;
+    return SKIRT_OK;
+}
+
+extern "C" int skirt_mlp_get_guard(skirt_mlp_t net, float* share_max)
+{
+    if (!net || !share_max) return set_error(SKIRT_ERR_INVALID_ARG, "net / share_max is NULL");
+    *share_max = net->share_max;
+    return SKIRT_OK;
+}
+
 extern "C" int skirt_mlp_get_params(skirt_mlp_t net, float* params, float* x_mean, float* x_std, float* hull_lo,
                                     float* hull_hi)
 {
@@ -588,6 +633,7 @@ extern "C" int skirt_mlp_train_opts_default(skirt_mlp_train_opts* o)
     o->beta2 = 0.999f;
     o->eps = 1e-8f;
     o->seed = 1;
+    o->guard_quantile = 0.99f;
     return SKIRT_OK;
 }
 
@@ -696,6 +742,7 @@ extern "C" int skirt_mlp_train(skirt_mlp_t net, const float* features, const dou
     const int B = opts->batch;
     if (B < 32 || B > (1 << 16) || n < B) return set_error(SKIRT_ERR_INVALID_ARG, "batch must be in [32, 65536] and <= n");
     if (opts->epochs < 1 || !(opts->lr > 0)) return set_error(SKIRT_ERR_INVALID_ARG, "epochs / lr invalid");
+    if (!(opts->guard_quantile > 0.f)) return set_error(SKIRT_ERR_INVALID_ARG, "guard_quantile must be > 0");
     cudaStream_t s = (cudaStream_t)stream;
     TrainScope sc(s);
     // target shapes: every emission row normalised to sum 1
@@ -720,6 +767,21 @@ extern "C" int skirt_mlp_train(skirt_mlp_t net, const float* features, const dou
         net->host_stats[3 * NIN + k] = (float)st[4 * k + 3];
     }
     if (int r = upload_stats(net)) return r;
+    // the guard: the guard_quantile quantile of the training rows' dominant-band share
+    if (opts->guard_quantile >= 1.f) {
+        net->share_max = 1.f;
+    } else {
+        float*& d_share = sc.x_in;
+        MCK(cudaMallocAsync((void**)&d_share, sizeof(float) * (size_t)n, s));
+        dominant_share_kernel<<<blocks_for(n, 256), 256, 0, s>>>(features, n, d_share);
+        MCK(cudaGetLastError());
+        std::vector<float> sh((size_t)n);
+        MCK(cudaMemcpyAsync(sh.data(), d_share, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, s));
+        MCK(cudaStreamSynchronize(s));
+        const size_t k = (size_t)((double)opts->guard_quantile * (double)(n - 1));
+        std::nth_element(sh.begin(), sh.begin() + k, sh.end());
+        net->share_max = sh[k];
+    }
     MCK(cudaMemsetAsync(net->Mo, 0, sizeof(float) * NPARAM, s));
     MCK(cudaMemsetAsync(net->Vo, 0, sizeof(float) * NPARAM, s));
     Work& w = sc.w;

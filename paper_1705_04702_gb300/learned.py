@@ -84,6 +84,7 @@ def run_learned(n=256, nlambda=200, packet_scale=1.0, n_train=1_000_000, n_test=
     _sync()
     rep["t_training"] = time.perf_counter() - t0
     rep["n_train"], rep["n_test"] = n_train, n_test
+    rep["guard_share_max"] = net.get_guard()
     rep["loss_first_last"] = [float(hist[0]), float(hist[-1])]
     del a_tr, ex_tr
 

@@ -55,17 +55,18 @@ TUNE_MAX_POINTS = 256
 
 class skirt_tune_point(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int), ("chunk", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
-                ("step_min", ctypes.c_int), ("ms", ctypes.c_float)]
+                ("step_min", ctypes.c_int), ("ms", ctypes.c_float), ("ms_confirm", ctypes.c_float)]
 
 
 class skirt_tune_report(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("chosen", ctypes.c_int), ("repeats", ctypes.c_int),
-                ("sample_packets", ctypes.c_ulonglong), ("points", skirt_tune_point * TUNE_MAX_POINTS)]
+                ("sample_packets", ctypes.c_ulonglong), ("confirm_packets", ctypes.c_ulonglong),
+                ("points", skirt_tune_point * TUNE_MAX_POINTS)]
 
     def as_dict(self):
         pts = [{k: getattr(self.points[i], k) for k, _ in skirt_tune_point._fields_} for i in range(self.n)]
         return {"n": self.n, "chosen": self.chosen, "repeats": self.repeats, "sample_packets": self.sample_packets,
-                "points": pts}
+                "confirm_packets": self.confirm_packets, "points": pts}
 
 
 class skirt_ledger(ctypes.Structure):
@@ -353,7 +354,7 @@ MLP_NPARAM = 128 * 32 + 128 + 128 * 128 + 128 + 100 * 128 + 100
 class skirt_mlp_train_opts(ctypes.Structure):
     _fields_ = [("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float),
                 ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("guard_quantile", ctypes.c_float)]
 
 
 class skirt_emission_stats(ctypes.Structure):
@@ -373,6 +374,8 @@ def _bind_emission(L):
     L.skirt_mlp_destroy.argtypes = [vp]
     L.skirt_mlp_set_params.argtypes = [vp, fp, fp, fp, fp, fp]
     L.skirt_mlp_get_params.argtypes = [vp, fp, fp, fp, fp, fp]
+    L.skirt_mlp_set_guard.argtypes = [vp, ctypes.c_float]
+    L.skirt_mlp_get_guard.argtypes = [vp, fp]
     L.skirt_mlp_train_opts_default.argtypes = [ctypes.POINTER(skirt_mlp_train_opts)]
     L.skirt_mlp_train.argtypes = [vp, vp, vp, ll, ctypes.POINTER(skirt_mlp_train_opts), fp, vp]
     L.skirt_mlp_grad.argtypes = [vp, vp, vp, i, fp, fp, vp]
@@ -382,7 +385,8 @@ def _bind_emission(L):
     L.skirt_dust_emission_pair.argtypes = [vp, ll, i, _dp, vp, i, _dp, vp, vp, vp, vp]
     L.skirt_emission_totals.argtypes = [vp, vp, i, _dp, vp]
     for name in ("skirt_emission_grid", "skirt_dust_mass", "skirt_band_features", "skirt_mlp_create",
-                 "skirt_mlp_destroy", "skirt_mlp_set_params", "skirt_mlp_get_params", "skirt_mlp_train_opts_default",
+                 "skirt_mlp_destroy", "skirt_mlp_set_params", "skirt_mlp_get_params", "skirt_mlp_set_guard",
+                 "skirt_mlp_get_guard", "skirt_mlp_train_opts_default",
                  "skirt_mlp_train", "skirt_mlp_grad", "skirt_mlp_forward", "skirt_dust_emission",
                  "skirt_dust_emission_exact_static", "skirt_dust_emission_pair", "skirt_emission_totals"):
         getattr(L, name).restype = i
@@ -482,7 +486,16 @@ class MLP:
                "skirt_mlp_get_params")
         return out  # params, mean, std, lo, hi
 
-    def train(self, features, emission, n, epochs=None, batch=None, lr=None, seed=None, stream=None):
+    def set_guard(self, share_max):
+        _check(lib.skirt_mlp_set_guard(self.h, float(share_max)), "skirt_mlp_set_guard")
+
+    def get_guard(self):
+        v = ctypes.c_float()
+        _check(lib.skirt_mlp_get_guard(self.h, ctypes.byref(v)), "skirt_mlp_get_guard")
+        return v.value
+
+    def train(self, features, emission, n, epochs=None, batch=None, lr=None, seed=None, stream=None,
+              guard_quantile=None):
         """features: device float [n, 32]; emission: device double [n, 100]
         (target rows, normalised on the device)."""
         target = emission
@@ -496,6 +509,8 @@ class MLP:
             o.lr = float(lr)
         if seed is not None:
             o.seed = int(seed)
+        if guard_quantile is not None:
+            o.guard_quantile = float(guard_quantile)
         hist = np.zeros(o.epochs, np.float32)
         _check(lib.skirt_mlp_train(self.h, _ptr(features), _ptr(target), int(n), ctypes.byref(o),
                                    hist.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _st(stream)), "skirt_mlp_train")

@@ -34,6 +34,8 @@ tolerances"):
   distribution of the number of scatterings must be the oracle's
   (chi-square homogeneity, scattering_counts_agree()).
 """
+import math
+
 import numpy as np
 
 REL_FP64 = 1e-9
@@ -259,15 +261,24 @@ def packet_tallies_gpu(S, grid, prob, pairs, bins, template, precision, **run_kw
     return acc, sq
 
 
-def split_check(gpu_tot, ref_tot, gpu_f, ref_f, gpu_f2, ref_f2, rel, significant, k=K_SIGMA):
+# The mixed form ends a deposit or peel-off traversal once its optical depth
+# passes 30 and drops contributions below the FP32 range (design reading
+# 11): a packet loses at most e^-30 of its luminosity per traversal, so an
+# entry can differ by up to this share of the luminosity of the packets
+# behind it, times the traversals of a packet (bounded here by 100).
+CUT_SHARE = 100 * math.exp(-30.0)
+
+
+def split_check(gpu_tot, ref_tot, gpu_f, ref_f, gpu_f2, ref_f2, rel, significant, k=K_SIGMA, atol=0.0):
     """gpu_tot / ref_tot: tallies of all packets; gpu_f / ref_f: the sums of
     the unmatched packets' own tallies, gpu_f2 / ref_f2 their sums of
     squares.  The matched packets' part (total minus unmatched) must agree
     within rel (entries >= significant of the total, and L1); the unmatched
     part must differ by at most k standard deviations of the difference of two
     independent samples of those packets, sqrt(gpu_f2 + ref_f2), entry by
-    entry and summed over all entries.  Returns (matched part's L1, unmatched
-    part's L1 share of the total)."""
+    entry and summed over all entries, plus atol (the optical-depth cut-off's
+    share of those packets' luminosity, CUT_SHARE).  Returns (matched part's
+    L1, unmatched part's L1 share of the total)."""
     g = np.asarray(gpu_tot, np.float64).ravel()
     r = np.asarray(ref_tot, np.float64).ravel()
     gf = np.asarray(gpu_f, np.float64).ravel()
@@ -277,9 +288,10 @@ def split_check(gpu_tot, ref_tot, gpu_f, ref_f, gpu_f2, ref_f2, rel, significant
     l1 = compare_tally(g - gf, r - rf, rel, significant=significant)
     d = gf - rf
     sig = np.sqrt(var)
-    bad = np.abs(d) > k * sig + 1e-12 * np.abs(r)
+    bad = np.abs(d) > k * sig + 1e-12 * np.abs(r) + atol
     assert not bad.any(), ("unmatched packets beyond k sigma", int(bad.sum()), d[bad][:5], sig[bad][:5])
-    assert abs(d.sum()) <= k * np.sqrt(var.sum()) + 1e-12 * abs(r.sum()), (d.sum(), np.sqrt(var.sum()))
+    assert abs(d.sum()) <= k * np.sqrt(var.sum()) + 1e-12 * abs(r.sum()) + atol * d.size, (d.sum(),
+                                                                                          np.sqrt(var.sum()))
     return l1, float(np.abs(d).sum() / max(np.abs(r).sum(), 1e-300))
 
 
@@ -312,18 +324,20 @@ def check_mixed(S, oracle_lib, grid, prob, g, r, chaotic=False, min_match=0.999,
     bins = [rebin_factor(prob, ins) for ins in prob.instruments]
     template = _parts(r["absorbed"], r["sed"], r["images"], bins)
     pairs = np.argwhere(um)
+    L0, _, _ = record_scales(prob)
+    cut = CUT_SHARE * float(sum(L0[j] for j, _ in pairs))  # the unmatched packets' luminosity
     gf, gf2 = packet_tallies_gpu(S, grid, prob, pairs, bins, template, S.PREC_MIXED, **gpu_kw)
     of, of2 = packet_tallies_oracle(oracle_lib, prob, pairs, bins, template, **oracle_kw)
     out["absorbed"] = split_check(g["absorbed"].cpu().numpy(), r["absorbed"], gf["absorbed"], of["absorbed"],
-                                  gf2["absorbed"], of2["absorbed"], REL_MIXED_TALLY, significant)
+                                  gf2["absorbed"], of2["absorbed"], REL_MIXED_TALLY, significant, atol=cut)
     if prob.instruments:
         out["sed"] = split_check(g["sed"].cpu().numpy(), r["sed"], gf["sed"], of["sed"], gf2["sed"], of2["sed"],
-                                 REL_MIXED_TALLY, 0.0)
+                                 REL_MIXED_TALLY, 0.0, atol=cut)
         for q in range(len(prob.instruments)):
             gi = rebin(g["images"][q].cpu().numpy(), bins[q])
             ri = rebin(r["images"][q], bins[q])
             out[f"image{q}"] = split_check(gi, ri, gf["images"][q], of["images"][q], gf2["images"][q],
-                                           of2["images"][q], REL_MIXED_TALLY, significant)
+                                           of2["images"][q], REL_MIXED_TALLY, significant, atol=cut)
     # the ledger per wavelength: emitted, absorbed, escaped, residual; the
     # unmatched packets' shares come from their records
     um_g = np.stack([np.where(um, gr[..., f], 0.0).sum(axis=1) for f in (2, 1, 3)], axis=1)
@@ -373,13 +387,16 @@ def record_sigma_check(gpu, ref, prob, mask, k=K_SIGMA):
     packets' own shares of the ledger and of the SEDs): over the packets in
     mask, the summed GPU-minus-oracle difference per wavelength and over all
     wavelengths stays within k standard deviations of the difference of two
-    independent samples (sqrt of the summed squares of both)."""
+    independent samples (sqrt of the summed squares of both), plus the
+    optical-depth cut-off's share (CUT_SHARE) of those packets' luminosity."""
     gpu = np.asarray(gpu, np.float64)
     ref = np.asarray(ref, np.float64)
+    L0, norm, _ = record_scales(prob)
     for f in (1, 2, 3, 4):
         g = np.where(mask, gpu[..., f], 0.0)
         r = np.where(mask, ref[..., f], 0.0)
         d = (g - r).sum(axis=1)
         sig = np.sqrt((g ** 2 + r ** 2).sum(axis=1))
-        assert np.all(np.abs(d) <= k * sig + 1e-300), ("field", f, d, sig)
-        assert abs(d.sum()) <= k * np.sqrt((sig ** 2).sum()) + 1e-300, ("field", f, d.sum())
+        cut = CUT_SHARE * L0 * mask.sum(axis=1) * (norm if f == 4 else 1.0)
+        assert np.all(np.abs(d) <= k * sig + cut + 1e-300), ("field", f, d, sig)
+        assert abs(d.sum()) <= k * np.sqrt((sig ** 2).sum()) + cut.sum() + 1e-300, ("field", f, d.sum())

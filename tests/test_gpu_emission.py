@@ -135,6 +135,19 @@ def test_tensor_core_inference_matches_oracle(S):
     f = flags.cpu().numpy()
     expect = np.any((x < lo) | (x > hi), axis=1)
     assert np.array_equal(f.astype(bool), expect) and f[5] == 1 and f[9] == 1
+    # the guard on the dominant band's share: flags follow the oracle's share,
+    # except within FP32 rounding of the threshold (the kernel sums 10^(f - max)
+    # in FP32 in another order), where either decision is right
+    share = E.dominant_share(x)
+    thr = float(np.quantile(share, 0.8))
+    net.set_guard(thr)
+    assert net.get_guard() == pytest.approx(thr, rel=1e-7)
+    flags.zero_()
+    net.forward(_dev(x, torch.float32), _dev(tot, torch.float64), n, em, flags)
+    f = flags.cpu().numpy().astype(bool)
+    expect = np.any((x < lo) | (x > hi), axis=1) | (share > np.float32(thr))
+    tie = np.abs(share / np.float32(thr) - 1.0) < 1e-5
+    assert np.array_equal(f[~tie], expect[~tie]) and expect.sum() > 150
     net.close()
 
 
@@ -174,6 +187,13 @@ def test_training_reaches_two_percent_and_fallback_is_exact(S):
     assert st2["n_fallback"] == 50
     ref2, _, _ = E.exact_emission(a2, lam, m[n_train:n_train + 50].astype(np.float64))
     np.testing.assert_allclose(em2.cpu().numpy(), ref2, rtol=1e-9, atol=1e-12 * ref2.max())
+    # the guard: the 99th percentile of the training rows' dominant-band share
+    share_tr = E.dominant_share(feat[:n_train].cpu().numpy())
+    k = int(0.99 * (n_train - 1))
+    assert net.get_guard() == pytest.approx(np.partition(share_tr, k)[k], rel=1e-5)
+    share_te = E.dominant_share(feat[n_train:].cpu().numpy())
+    guarded = share_te > net.get_guard()
+    assert abs(st["n_fallback"] - int(guarded.sum())) <= max(3, int(0.1 * guarded.sum()) + 3), st["n_fallback"]
     net.close()
 
 

@@ -304,8 +304,11 @@ def test_autotune_picks_a_swept_schedule_with_identical_histories(S):
     c = pts[rep["chosen"]]
     assert (opts.block, opts.chunk, opts.blocks_per_sm, opts.step_min) == (c["block"], c["chunk"],
                                                                           c["blocks_per_sm"], c["step_min"])
-    assert c["ms"] <= pts[0]["ms"]
     assert all(p["ms"] > 0 for p in pts)
+    confirmed = [p for p in pts if p["ms_confirm"] > 0]
+    assert pts[0]["ms_confirm"] > 0 and c["ms_confirm"] > 0 and 2 <= len(confirmed) <= 4
+    assert c["ms_confirm"] <= pts[0]["ms_confirm"]
+    assert rep["confirm_packets"] > rep["sample_packets"] or rep["confirm_packets"] == int(prob.npk.sum())
     nrec = int(prob.npk.max())
     base = S.run_problem(prob, grid, nrec=nrec)
     tuned = S.run_problem(prob, grid, nrec=nrec, block=opts.block, chunk=opts.chunk,

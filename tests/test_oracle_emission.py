@@ -127,6 +127,17 @@ def test_band_features_floor_of_empty_bands():
     np.testing.assert_array_equal(tot, [2.0, 4.0, 1.0, 0.0])
 
 
+def test_dominant_share_by_hand():
+    """The guard's quantity on rows computed by hand: two equal bands and the
+    rest empty (-30) -> 1/2; 32 equal bands -> 1/32; one band at 10x another
+    (log10 difference 1), the rest empty -> 10/11."""
+    x = np.full((3, 32), -30.0)
+    x[0, :2] = 1.5
+    x[1, :] = -2.0
+    x[2, 4], x[2, 9] = 0.5, -0.5
+    np.testing.assert_allclose(E.dominant_share(x), [0.5, 1.0 / 32, 10.0 / 11.0], rtol=1e-14)
+
+
 def _params(rng, scale=0.3):
     return {"W1": rng.normal(size=(128, 32)) * scale, "b1": rng.normal(size=128) * 0.1,
             "W2": rng.normal(size=(128, 128)) * scale / 3, "b2": rng.normal(size=128) * 0.1,
