@@ -229,8 +229,9 @@ def test_learned_form_full_grid_sampled(S, oracle_lib):
     wavelengths; the absorbed table from a 5% stellar trace): band features
     and the exact emission on every cell, the oracle on 2000 sampled heated
     cells; energy exact on every cell; the surrogate (trained on 500k cells,
-    60 epochs) energy-exact on every cell and within 2% of the exact rows
-    (median)."""
+    60 epochs) energy-exact on every cell; on every heated cell, after the
+    guard's fallback, the median and the 99th percentile of the per-cell
+    error within 2% of the exact rows (the largest error is reported)."""
     import torch
     from oracle import emission as E
     prob = W.torus_problem(n=256, nlambda=200, npx=64, packet_scale=0.05)
@@ -278,6 +279,9 @@ def test_learned_form_full_grid_sampled(S, oracle_lib):
     assert st["n_cells"] == ncell
     rs = (sur.index_select(0, live).sum(dim=1) - tot.index_select(0, live)).abs() / tot.index_select(0, live)
     assert float(rs.max()) < 1e-5
-    e = (torch.linalg.vector_norm(sur.index_select(0, pick) - exact.index_select(0, pick), dim=1) /
-         torch.linalg.vector_norm(exact.index_select(0, pick), dim=1)).cpu().numpy()
-    assert np.median(e) < 0.02, np.median(e)
+    e = (torch.linalg.vector_norm(sur.index_select(0, live) - exact.index_select(0, live), dim=1) /
+         torch.linalg.vector_norm(exact.index_select(0, live), dim=1)).cpu().numpy()
+    print("surrogate error over the heated cells: median", np.median(e), "p99", np.percentile(e, 99), "max", e.max(),
+          "fallback", st["n_fallback"], "within 2%", (e <= 0.02).mean())
+    assert st["n_fallback"] > 0
+    assert np.median(e) < 0.02 and np.percentile(e, 99) < 0.02, (np.median(e), np.percentile(e, 99))
