@@ -647,11 +647,10 @@ def main():
         h2d = h_kr.numel() * 4
         d2h = (h_abs.numel() + h_img.numel() + h_sed.numel()) * 8
         if octree:
-            # grid creation uploads the node heads (8 B per node, 8 + 8 (nleaf - 1) / 7 nodes at most) and
-            # the leaf table (16 B per leaf), and reads kr back once (4 B per leaf); the face neighbours
-            # are found on the device
+            # grid creation uploads the node array (32 B per node, 1 + 8 (nleaf - 1) / 7 nodes), the
+            # leaf table (16 B) and the leaf-to-node map (4 B), and reads kr back once (4 B per leaf)
             nl = prob.grid.ncell
-            h2d += 8 * (8 + 8 * (nl - 1) // 7) + 16 * nl
+            h2d += 32 * (1 + 8 * (nl - 1) // 7) + 20 * nl
             d2h += 4 * nl
         e2e = {"value": packets * world / dte, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": ksteps}

@@ -257,8 +257,7 @@ extern "C" int skirt_grid_destroy(skirt_grid_t g)
     if (g->kr32) cudaFree(g->kr32);
     if (g->kr64) cudaFree(g->kr64);
     if (g->faces) cudaFree(g->faces);
-    if (g->oct_head) cudaFree(g->oct_head);
-    if (g->oct_nb) cudaFree(g->oct_nb);
+    if (g->oct_nodes) cudaFree(g->oct_nodes);
     if (g->oct_leaf) cudaFree(g->oct_leaf);
     g->scratch.release();
     g->stage.release();
@@ -479,8 +478,7 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
     A.nx = g->nx; A.ny = g->ny; A.nz = g->nz;
     A.ncell = g->ncell;
     A.oct_levels = g->oct_levels;
-    A.oct_head = g->oct_head;
-    A.oct_nb = g->oct_nb;
+    A.oct_nodes = g->oct_nodes;
     A.oct_leaf = g->oct_leaf;
     A.oct_step_cap = g->nx + g->ny + g->nz + 8;
     const int nn[3] = {g->nx, g->ny, g->nz};

@@ -2,11 +2,11 @@
 // octree grid with up to 13 division levels and 8.2 million cells).
 //
 // The caller lists the leaves (level and integer position at that level);
-// the host inserts them from the root down into an array of 8-byte node heads
-// (children of a node are 8 consecutive nodes) and checks that they tile the
-// root box; a kernel then finds, for every leaf and each of its 6 faces, the
-// node across that face: the node of the same level if the tree has one, else
-// the leaf of a larger size that covers it (a per-leaf table).  A traversal (trace.cu) crosses a face by
+// the host inserts them from the root down into a node array (children of a
+// node are 8 consecutive nodes) and checks that they tile the root box; a
+// kernel then finds, for every leaf and each of its 6 faces, the node across
+// that face: the node of the same level if the tree has one, else the leaf
+// of a larger size that covers it.  A traversal (trace.cu) crosses a face by
 // reading that neighbour and, when the neighbour is split further, descending
 // from it by the finest-lattice cell of the entry point.
 #include <cuda_runtime.h>
@@ -22,7 +22,8 @@ namespace {
 // One thread per leaf: the neighbour across each face, found by descending
 // from the root towards the same-level box on the other side, stopping at a
 // leaf (a larger one covers that box) or at the same level.
-__global__ void oct_neighbours_kernel(const OctHead* heads, int* nbs, const int4* leaf, long long nleaf, int levels)
+__global__ void oct_neighbours_kernel(OctNode* nodes, const int4* leaf, const int* leaf_node, long long nleaf,
+                                      int levels)
 {
     for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < nleaf;
          m += (long long)gridDim.x * blockDim.x) {
@@ -30,6 +31,7 @@ __global__ void oct_neighbours_kernel(const OctHead* heads, int* nbs, const int4
         const int lev = lf.w, sh = levels - lev;
         const int c[3] = {lf.x >> sh, lf.y >> sh, lf.z >> sh};
         const int n = 1 << lev;
+        int nb[6];
         for (int f = 0; f < 6; ++f) {
             int q[3] = {c[0], c[1], c[2]};
             q[f >> 1] += (f & 1) ? 1 : -1;
@@ -37,16 +39,19 @@ __global__ void oct_neighbours_kernel(const OctHead* heads, int* nbs, const int4
             if (q[f >> 1] >= 0 && q[f >> 1] < n) {
                 node = 0;
                 for (int d = 0; d < lev; ++d) {
-                    const int r = heads[node].ref;
+                    const int r = nodes[node].ref;
                     if (r < 0) break;
                     const int b = lev - 1 - d;
                     node = r + (((q[0] >> b) & 1) | (((q[1] >> b) & 1) << 1) | (((q[2] >> b) & 1) << 2));
                 }
             }
-            nbs[6 * m + f] = node;
+            nb[f] = node;
         }
+        OctNode* me = nodes + leaf_node[m];
+        for (int f = 0; f < 6; ++f) me->nb[f] = nb[f];
     }
 }
+
 }  // namespace
 }  // namespace skirt
 
@@ -119,28 +124,33 @@ extern "C" int skirt_octree_create(skirt_grid_t* out, int max_level, const doubl
     cudaError_t e;
     if ((e = cudaMemcpy(krh.data(), g->kr32, sizeof(float) * (size_t)nleaf, cudaMemcpyDeviceToHost)) != cudaSuccess)
         return bail(set_error(SKIRT_ERR_CUDA, "copy kr: %s", cudaGetErrorString(e)));
-    std::vector<OctHead> heads(ref.size());
+    std::vector<OctNode> nodes(ref.size());
     for (size_t i = 0; i < ref.size(); ++i) {
-        heads[i].ref = ref[i];
-        heads[i].kr = 0.f;
+        std::memset(&nodes[i], 0, sizeof(OctNode));
+        nodes[i].ref = ref[i];
+        for (int f = 0; f < 6; ++f) nodes[i].nb[f] = -1;
     }
-    for (long long m = 0; m < nleaf; ++m) heads[(size_t)leaf_node[(size_t)m]].kr = krh[(size_t)m];
+    for (long long m = 0; m < nleaf; ++m) nodes[(size_t)leaf_node[(size_t)m]].kr = krh[(size_t)m];
 
+    int* d_leaf_node = nullptr;
     auto upload = [&](void** dst, const void* src, size_t bytes) -> cudaError_t {
         cudaError_t r = cudaMalloc(dst, bytes);
         if (r != cudaSuccess) return r;
         return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
     };
-    if ((e = upload((void**)&g->oct_head, heads.data(), sizeof(OctHead) * heads.size())) != cudaSuccess ||
+    if ((e = upload((void**)&g->oct_nodes, nodes.data(), sizeof(OctNode) * nodes.size())) != cudaSuccess ||
         (e = upload((void**)&g->oct_leaf, leaf_tab.data(), sizeof(int4) * leaf_tab.size())) != cudaSuccess ||
-        (e = cudaMalloc((void**)&g->oct_nb, sizeof(int) * 6 * (size_t)nleaf)) != cudaSuccess)
+        (e = upload((void**)&d_leaf_node, leaf_node.data(), sizeof(int) * leaf_node.size())) != cudaSuccess) {
+        if (d_leaf_node) cudaFree(d_leaf_node);
         return bail(set_error(e == cudaErrorMemoryAllocation ? SKIRT_ERR_OOM : SKIRT_ERR_CUDA, "octree upload: %s",
                               cudaGetErrorString(e)));
+    }
     long long blocks = (nleaf + 255) / 256;
     if (blocks > 4096) blocks = 4096;
-    oct_neighbours_kernel<<<(int)blocks, 256>>>(g->oct_head, g->oct_nb, g->oct_leaf, nleaf, max_level);
+    oct_neighbours_kernel<<<(int)blocks, 256>>>(g->oct_nodes, g->oct_leaf, d_leaf_node, nleaf, max_level);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(d_leaf_node);
     if (e != cudaSuccess) return bail(set_error(SKIRT_ERR_CUDA, "octree neighbours: %s", cudaGetErrorString(e)));
     *out = g;
     return SKIRT_OK;

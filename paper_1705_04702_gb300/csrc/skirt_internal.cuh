@@ -46,18 +46,17 @@ struct InstrDev {
 
 enum { ERRBIT_EVENT_CAP = 1, ERRBIT_SOURCE = 2, ERRBIT_NONFINITE = 4, ERRBIT_PATH = 8 };
 
-// Octree node head (8 bytes): ref >= 0: internal node whose 8 children are
-// nodes ref .. ref+7 (octant x + 2y + 4z; ref is a multiple of 8, node 0 is
-// the root and nodes 1..7 are unused); ref < 0: a leaf, ~ref = level << 27 |
-// leaf index (levels up to 15).  kr: the leaf's extinction coefficient.  The
-// heads of a tree of 9.4M nodes take 75 MB, within the L2.  The face
-// neighbours live apart, per leaf: nb[6 leaf + 2a + (positive side)] is the
-// node across that face along axis a of the same level, or the leaf of a
-// larger size that covers it (-1 outside the root box); a crossing reads it
-// only when it leaves the leaf's parent.
-struct __align__(8) OctHead {
+// Octree node (32 bytes, one sector).  ref >= 0: internal node whose 8
+// children are nodes ref .. ref+7 (octant x + 2y + 4z; ref is a multiple of
+// 8, node 0 is the root and nodes 1..7 are unused); ref < 0: a leaf,
+// ~ref = level << 27 | leaf index (levels up to 15).  kr: the leaf's extinction coefficient.
+// nb[2a + (positive side)]: for a leaf, the node across that face along
+// axis a of the same level, or the leaf of a larger size that covers it
+// (-1 outside the root box).
+struct __align__(16) OctNode {
     int ref;
     float kr;
+    int nb[6];
 };
 constexpr int OCT_LEAF_BITS = 27;
 __host__ __device__ __forceinline__ int oct_leaf_index(int ref) { return (~ref) & ((1 << OCT_LEAF_BITS) - 1); }
@@ -113,8 +112,7 @@ struct TraceArgs {
     // octree grid (oct_levels > 0): nx = ny = nz = 2^oct_levels is the finest
     // lattice, d its cell size; cells are leaves
     int oct_levels;
-    const OctHead* oct_head;               // node heads
-    const int* oct_nb;                     // per leaf: the 6 face neighbours
+    const OctNode* oct_nodes;
     const int4* oct_leaf;                  // per leaf: lattice corner x, y, z and level
     int oct_step_cap;                      // crossings after which a traversal is abandoned
 };
@@ -225,8 +223,7 @@ struct skirt_grid_s {
     skirt::DevBuf abs_lmajor;  // wavelength-major absorbed table of the current call
     int oct_levels = 0;              // octree grid: finest lattice 2^oct_levels per axis
     long long oct_nnode = 0;
-    skirt::OctHead* oct_head = nullptr;
-    int* oct_nb = nullptr;
+    skirt::OctNode* oct_nodes = nullptr;
     int4* oct_leaf = nullptr;        // per leaf: lattice corner and level
     skirt::PinnedBuf pinned;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;

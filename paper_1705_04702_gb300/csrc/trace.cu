@@ -116,17 +116,17 @@ __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A)
     // octree: the leaf holding lattice cell (j0, j1, j2), found by descending
     // from `node` (a node of level `lev`, or a leaf)
     auto oct_enter = [&](int node, int lev, int j0, int j1, int j2) {
-        int2 h = __ldg(reinterpret_cast<const int2*>(A.oct_head + node));
-        while (h.x >= 0 && lev < OL) {
+        int r = __ldg(&A.oct_nodes[node].ref);
+        while (r >= 0 && lev < OL) {
             ++lev;
             const int b = OL - lev;
-            node = h.x + (((j0 >> b) & 1) | (((j1 >> b) & 1) << 1) | (((j2 >> b) & 1) << 2));
-            h = __ldg(reinterpret_cast<const int2*>(A.oct_head + node));
+            node = r + (((j0 >> b) & 1) | (((j1 >> b) & 1) << 1) | (((j2 >> b) & 1) << 2));
+            r = __ldg(&A.oct_nodes[node].ref);
         }
         onode = node;
-        olev = oct_leaf_level(h.x);
-        oleaf = oct_leaf_index(h.x);
-        okr = __int_as_float(h.y);
+        olev = oct_leaf_level(r);
+        oleaf = oct_leaf_index(r);
+        okr = __ldg(&A.oct_nodes[node].kr);
         const int mask = ~((1 << (OL - olev)) - 1);
         c0 = j0 & mask;
         c1 = j1 & mask;
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(512) trace_kernel(const TraceArgs A)
             if (!done && OCT) {
                 tcur = tnext;
                 const int sa = axis == 0 ? s0 : (axis == 1 ? s1 : s2);
-                const int nb = __ldg(A.oct_nb + 6 * (size_t)oleaf + 2 * axis + (sa > 0));
+                const int nb = __ldg(&A.oct_nodes[onode].nb[2 * axis + (sa > 0)]);
                 if (nb < 0) {
                     done = true;  // the exit face lies on the root box
                 } else if (++osteps > A.oct_step_cap) {

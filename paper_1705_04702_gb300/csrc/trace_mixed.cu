@@ -182,8 +182,7 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
     // octree: the current leaf's node and level (c0..c2: its lattice corner),
     // the traversal direction, the node of the interaction leaf
     const int OL = A.oct_levels;
-    const OctHead* __restrict__ heads = A.oct_head;
-    const int* __restrict__ nbs = A.oct_nb;
+    const OctNode* __restrict__ nodes = A.oct_nodes;
     const float id0 = 1.f / d0, id1 = 1.f / d1, id2 = 1.f / d2;
     int onode = 0, olev = 0, pc_node = 0;
     float v0 = 0.f, v1 = 0.f, v2 = 0.f;
@@ -207,12 +206,12 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
     // octree: enter the leaf holding lattice cell (j0, j1, j2), descending
     // from `node` (a leaf, or a node of level `lev`)
     auto oct_enter = [&](int node, int lev, int j0, int j1, int j2) {
-        int2 h = __ldg(reinterpret_cast<const int2*>(heads + node));
+        int2 h = __ldg(reinterpret_cast<const int2*>(nodes + node));
         while (h.x >= 0 && lev < OL) {
             ++lev;
             const int b = OL - lev;
             node = h.x + (((j0 >> b) & 1) | (((j1 >> b) & 1) << 1) | (((j2 >> b) & 1) << 2));
-            h = __ldg(reinterpret_cast<const int2*>(heads + node));
+            h = __ldg(reinterpret_cast<const int2*>(nodes + node));
         }
         onode = node;
         olev = oct_leaf_level(h.x);
@@ -270,9 +269,9 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
         // from the leaf's own (children blocks start at multiples of 8);
         // only a face on the parent's boundary needs the stored neighbour
         const bool inner = olev > 0 && ((onode >> axis) & 1) == (ss < 0 ? 1 : 0);
-        const int nb = inner ? onode ^ (1 << axis) : __ldg(nbs + 6 * (size_t)cur_m + 2 * axis + (ss > 0));
+        const int nb = inner ? onode ^ (1 << axis) : __ldg(&nodes[onode].nb[2 * axis + (ss > 0)]);
         const bool out = nb < 0;
-        const int2 nbh = out ? make_int2(0, 0) : __ldg(reinterpret_cast<const int2*>(heads + nb));
+        const int2 nbh = out ? make_int2(0, 0) : __ldg(reinterpret_cast<const int2*>(nodes + nb));
         const float ds = fmaxf(tmin - tcur, 0.f);
         const int m = cur_m;
         const float krl = kr_cur * krs;
