@@ -556,8 +556,11 @@ int launch_exact_emission(const double* absorbed, int n_in, const double* w_dev,
                           cudaStream_t s, const double* absorbed2, int n2, const double* w2_dev)
 {
     ECK(upload_model(s));
-    // a short row list: one warp per row keeps the Newton solves' latency short
-    if (rows && nrows > 0 && nrows <= 8192)
+    // a row list (the surrogate's fallback rows): one warp per row.  The FP64
+    // work per row is the same as with a thread per row, spread over the lanes,
+    // and a list of ~1e5 rows then still gives every SM enough warps to keep
+    // its FP64 pipe busy (a thread per row would leave ~20 warps per SM)
+    if (rows && nrows > 0)
         exact_warp_kernel<<<(int)((nrows + 3) / 4), 128, 0, s>>>(absorbed, n_in, w_dev, absorbed2, n2, w2_dev, mass,
                                                                 rows, nrows, emission, temperature);
     else if (nrows > 0)
