@@ -316,3 +316,25 @@ def test_autotune_picks_a_swept_schedule_with_identical_histories(S):
     assert np.array_equal(_np(base["records"]), _np(tuned["records"]))
     compare_tally(_np(tuned["absorbed"]), _np(base["absorbed"]), 1e-12)
     grid.close()
+
+
+@pytest.mark.parametrize("chaotic", [False, True], ids=["sphere", "torus"])
+def test_parity_criterion_detects_a_planted_mistake(S, oracle_lib, chaotic):
+    """The mixed-form criterion has power: the oracle, run on the same packets
+    of a problem whose albedo is 5% higher (a mistake planted in the oracle's
+    input, on the CPU), fails check_mixed against the GPU's run of the right
+    problem, in a smooth medium and in the clumpy torus."""
+    import dataclasses
+    if chaotic:
+        prob = W.torus_problem(n=32, nlambda=4, packet_scale=5e-5, npx=32)
+    else:
+        prob = W.sphere_problem(20000)
+    wrong = dataclasses.replace(prob, wl=dataclasses.replace(prob.wl, albedo=np.minimum(prob.wl.albedo * 1.05,
+                                                                                         1.0)))
+    nrec = int(prob.npk.max())
+    grid = S.Grid(prob.grid)
+    g = S.run_problem(prob, grid, precision=S.PREC_MIXED, nrec=nrec)
+    r = oracle_lib.trace(wrong, nrec=nrec)
+    with pytest.raises(AssertionError):
+        check_mixed(S, oracle_lib, grid, prob, g, r, chaotic=chaotic)
+    grid.close()

@@ -78,3 +78,38 @@ def test_transparent_dust_converges_at_once(case):
     assert r["cycles"] == 2 and r["converged"]
     assert h[0]["absorbed"] < 1e-6 * h[0]["emitted"]
     assert h[1]["emitted"] == pytest.approx(h[0]["emitted"], rel=1e-6)
+
+
+def test_batched_cycles_trace_the_same_packets(case, run):
+    """The batch-means option splits every cycle's packets into disjoint
+    ranges: the same packets, so the same cycles and tables (to FP64
+    summation order); its variance estimate of a cycle's absorbed total
+    agrees with the one computed here from the per-packet absorbed records
+    of the last cycle (an independent estimate: sum over packets of the
+    squared deviations, n/(n-1) corrected, which the batch means approach
+    within their own sampling error)."""
+    import oracle
+    prob, A, mass, wl = case
+    b = OSA.self_absorption(prob.grid, A, prob.wl.lam, mass, PACKETS_PER_LAMBDA, SEED, tol=1e-2, max_cycles=12,
+                           wl=wl, batches=10)
+    assert b["cycles"] == run["cycles"]
+    for x, y in zip(b["history"], run["history"]):
+        assert x["absorbed"] == pytest.approx(y["absorbed"], rel=1e-12)
+        assert x["var_absorbed"] > 0
+    np.testing.assert_allclose(b["absorbed_dust"], run["absorbed_dust"], rtol=1e-12, atol=1e-300)
+    # the last cycle again, with a record of every packet
+    cdf, totals = OSA.cell_cdf(b["emission"])
+    npk = np.where(totals > 0, PACKETS_PER_LAMBDA, 0).astype(np.uint64)
+    last = _cycle_problem(prob, wl, totals, npk, len(b["history"]) - 1)
+    r = oracle.trace(last, peel=False, cell_cdf=cdf, nrec=PACKETS_PER_LAMBDA)
+    a = r["records"][..., 2][npk > 0].ravel()
+    var_packets = a.size / (a.size - 1.0) * np.sum((a - a.mean()) ** 2)
+    assert r["ledger"][:, 1].sum() == pytest.approx(b["history"][-1]["absorbed"], rel=1e-12)
+    # ten batches estimate a variance with a relative standard error of about sqrt(2/9) = 0.47
+    assert 0.2 < b["history"][-1]["var_absorbed"] / var_packets < 3.0
+
+
+def _cycle_problem(prob, wl, totals, npk, k):
+    from paper_1705_04702_gb300 import workloads as W
+    return W.Problem("cycle", prob.grid, W.Source(W.SRC_DUST), dataclasses.replace(wl, lsrc=totals), npk, [],
+                     seed=SEED, phase=OSA.PHASE0 + k)
