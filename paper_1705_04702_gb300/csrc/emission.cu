@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -38,8 +39,9 @@ __constant__ double c_lnG_lo[NPOP];     // ln G_i(3 K)
 __constant__ double c_lnG_hi[NPOP];     // ln G_i(2000 K)
 __constant__ double c_beta[NPOP];
 // ln G_i and d ln G_i / d ln T at NTAB log-spaced temperatures over [T_LO,
-// T_HI]: the starting point of the Newton solve (read through the L1 path)
-constexpr int NTAB = 128;
+// T_HI]: the starting point of the Newton solve (read through the L1 path);
+// 4096 intervals, so that every 2^k-th point also spans [T_LO, T_HI]
+constexpr int NTAB = 4097;
 __device__ double g_lnG_tab[NPOP][NTAB];
 __device__ double g_dlnG_tab[NPOP][NTAB];
 
@@ -206,143 +208,19 @@ int band_blocks(long long ncell)
     return (int)(b < 1 ? 1 : b);
 }
 
-// G_i(T) = sum_l K_il / expm1(a_l / T) and T dG/dT = sum K_il q x (1 + q)
-// (x_l = a_l / T is formed as a_l (1/T): one division per evaluation; the
-// output rows use the same K_il q_l products, so they sum to the power exactly)
-__device__ void pop_G(int i, double T, double& G, double& D)
-{
-    G = 0.0;
-    D = 0.0;
-    const double invT = 1.0 / T;
-    for (int l = 0; l < NOUT; ++l) {
-        const double x = c_a[l] * invT;
-        if (x > 700.0) continue;  // e^x overflows; the term is below 1e-300 of the largest
-        const double q = 1.0 / expm1(x);
-        const double t = c_K[i][l] * q;
-        G += t;
-        D += t * x * (1.0 + q);
-    }
-}
+// The exact solve runs one warp per row.  The three populations' terms
+// K_il / expm1(a_l / T_i) form NPOP * NOUT = 300 slots s = i * NOUT + l; lane
+// j holds slots lane + 32 k (k < EX_SLOTS) in registers.  A row costs one
+// evaluation of every population at its starting temperature (the table
+// start below is within a few 1e-14 of the root, so the Newton step there
+// already meets the 1e-13 convergence test), and the output terms are the
+// evaluation's own terms scaled by P_i / G_i: 300 FP64 expm1 per row, against
+// two evaluations per population plus a third pass for the output when the
+// solve starts from a coarse table.
+constexpr int NS = NPOP * NOUT;
+constexpr int EX_SLOTS = (NS + 31) / 32;
+constexpr int EX_WARPS = 4;  // warps per block
 
-// Starting point and bracket of the Newton solve for ln G_i(e^y) = target:
-// the table interval holding the target, and the cubic Hermite inverse of
-// ln G on it (slopes dy/d lnG = 1 / (d lnG / dy)), a few 1e-8 from the root.
-__device__ __forceinline__ void start_T(int i, double target, double& y, double& lo, double& hi)
-{
-    const double* tab = &g_lnG_tab[i][0];
-    int a = 0, b = NTAB - 1;  // tab[a] <= target < tab[b]
-    while (b - a > 1) {
-        const int mid = (a + b) >> 1;
-        if (__ldg(tab + mid) <= target) a = mid; else b = mid;
-    }
-    const double dy = (log(T_HI) - log(T_LO)) / (NTAB - 1);
-    lo = log(T_LO) + a * dy;
-    hi = lo + dy;
-    const double ga = __ldg(tab + a), gb = __ldg(tab + b);
-    const double h = gb - ga, u = (target - ga) / h;
-    const double sa = 1.0 / __ldg(&g_dlnG_tab[i][a]), sb = 1.0 / __ldg(&g_dlnG_tab[i][b]);
-    const double u2 = u * u, u3 = u2 * u;
-    y = (2.0 * u3 - 3.0 * u2 + 1.0) * lo + (u3 - 2.0 * u2 + u) * h * sa + (3.0 * u2 - 2.0 * u3) * hi +
-        (u3 - u2) * h * sb;
-    if (!(y > lo && y < hi)) y = 0.5 * (lo + hi);
-}
-
-// T_i solving c_i G_i(T) = P_i / M (ln_ratio = ln(P_i / M)) by Newton on
-// ln T from the table start, bisection inside the bracket when a step leaves
-// it; clamped to [T_LO, T_HI].  G_out receives G_i at the returned T (the
-// point of the last evaluation, whose Newton step was below 1e-13 relative),
-// so that emission rows normalised by it sum to P_i exactly.
-__device__ double solve_T(int i, double ln_ratio, double& G_out)
-{
-    const double target = ln_ratio - c_lnc[i];  // ln G at the solution
-    double G, D;
-    if (c_lnG_lo[i] - target >= 0.0 || c_lnG_hi[i] - target <= 0.0) {
-        const double T = c_lnG_lo[i] - target >= 0.0 ? T_LO : T_HI;
-        pop_G(i, T, G, D);
-        G_out = G;
-        return T;
-    }
-    double y, lo, hi;
-    start_T(i, target, y, lo, hi);
-    for (int it = 0; it < 100; ++it) {
-        const double T = exp(y);
-        pop_G(i, T, G, D);
-        const double f = log(G) - target;
-        if (f < 0.0) lo = y; else hi = y;
-        double y_new = y - f * G / D;
-        if (!(y_new > lo && y_new < hi)) y_new = 0.5 * (lo + hi);
-        if (fabs(y_new - y) <= 1e-13 * fabs(y)) {
-            G_out = G;
-            return T;
-        }
-        y = y_new;
-    }
-    const double T = exp(y);
-    pop_G(i, T, G, D);
-    G_out = G;
-    return T;
-}
-
-// Exact emission for rows m = rows ? rows[k] : k, k < nrows.  A second
-// absorbed table A2 [ncell][n2] with its shares w2 (may be NULL) adds its
-// power to each population's.
-__global__ void exact_kernel(const double* __restrict__ A, int n_in, const double* __restrict__ w,
-                             const double* __restrict__ A2, int n2, const double* __restrict__ w2,
-                             const float* __restrict__ mass, const unsigned* __restrict__ rows,
-                             long long nrows, double* __restrict__ emission, float* __restrict__ temperature)
-{
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nrows;
-         k += (long long)gridDim.x * blockDim.x) {
-        const long long m = rows ? (long long)rows[k] : k;
-        const double* row = A + (size_t)m * n_in;
-        double P[NPOP] = {0.0, 0.0, 0.0};
-        for (int j = 0; j < n_in; ++j) {
-            const double a = row[j];
-            P[0] += __ldg(w + j) * a;
-            P[1] += __ldg(w + n_in + j) * a;
-            P[2] += __ldg(w + 2 * n_in + j) * a;
-        }
-        if (A2) {
-            const double* row2 = A2 + (size_t)m * n2;
-            for (int j = 0; j < n2; ++j) {
-                const double a = row2[j];
-                P[0] += __ldg(w2 + j) * a;
-                P[1] += __ldg(w2 + n2 + j) * a;
-                P[2] += __ldg(w2 + 2 * n2 + j) * a;
-            }
-        }
-        const double M = (double)mass[m];
-        double T[NPOP], S[NPOP];
-        for (int i = 0; i < NPOP; ++i) {
-            T[i] = 0.0;
-            S[i] = 0.0;
-            if (P[i] > 0.0 && M > 0.0) T[i] = solve_T(i, log(P[i] / M), S[i]);
-        }
-        double* out = emission + (size_t)m * NOUT;
-        double invT[NPOP], PS[NPOP];
-        for (int i = 0; i < NPOP; ++i) {
-            invT[i] = S[i] > 0.0 ? 1.0 / T[i] : 0.0;
-            PS[i] = S[i] > 0.0 ? P[i] / S[i] : 0.0;
-        }
-        for (int l = 0; l < NOUT; ++l) {
-            double e = 0.0;
-            for (int i = 0; i < NPOP; ++i) {
-                if (S[i] > 0.0) {
-                    const double x = c_a[l] * invT[i];
-                    if (x <= 700.0) e += PS[i] * (c_K[i][l] * (1.0 / expm1(x)));
-                }
-            }
-            out[l] = e;
-        }
-        if (temperature)
-            for (int i = 0; i < NPOP; ++i) temperature[(size_t)m * NPOP + i] = (float)T[i];
-    }
-}
-
-// Warp-per-row form of exact_kernel, for short row lists (the surrogate's
-// fallback rows): the lanes split the wavelength sums, and every sum is
-// reduced and broadcast so that the Newton iteration stays warp-uniform.  Same
-// arithmetic as exact_kernel up to the order of the FP64 sums.
 __device__ __forceinline__ double warp_sum_bcast(double v)
 {
 #pragma unroll
@@ -350,108 +228,229 @@ __device__ __forceinline__ double warp_sum_bcast(double v)
     return __shfl_sync(0xffffffffu, v, 0);
 }
 
-__device__ void pop_G_warp(int i, double T, double& G, double& D, int lane)
+// term of slot s at 1/T: t = K_il q and its T dG/dT part t x (1 + q), with
+// q = 1 / expm1(x), x = a_l (1/T) (one division per evaluation); a term whose
+// e^x overflows (x > 700) is below 1e-300 of the largest and is left out
+__device__ __forceinline__ void slot_term(double a, double K, double invT, double& t, double& d)
+{
+    t = 0.0;
+    d = 0.0;
+    const double x = a * invT;
+    if (x <= 700.0) {
+        const double q = 1.0 / expm1(x);
+        t = K * q;
+        d = t * x * (1.0 + q);
+    }
+}
+
+// G_i and T dG_i/dT at T for one population, the lanes splitting the
+// wavelengths (the rare Newton solve that needs more than one evaluation)
+__device__ void pop_G_warp(int i, double T, double& G, double& D, int lane, const double* sa, const double* sK)
 {
     double g = 0.0, d = 0.0;
     const double invT = 1.0 / T;
     for (int l = lane; l < NOUT; l += 32) {
-        const double x = c_a[l] * invT;
-        if (x > 700.0) continue;
-        const double q = 1.0 / expm1(x);
-        const double t = c_K[i][l] * q;
+        double t, dd;
+        slot_term(sa[i * NOUT + l], sK[i * NOUT + l], invT, t, dd);
         g += t;
-        d += t * x * (1.0 + q);
+        d += dd;
     }
     G = warp_sum_bcast(g);
     D = warp_sum_bcast(d);
 }
 
-__device__ double solve_T_warp(int i, double ln_ratio, int lane, double& G_out)
+// Starting point and bracket of the Newton solve for ln G_i(e^y) = target:
+// the table interval holding the target (binary search), and the cubic
+// Hermite inverse of ln G on it (slopes dy/d lnG = 1 / (d lnG / dy)).  With
+// 4096 intervals over [ln 3, ln 2000] the start is within a few 1e-14 of the
+// root (the Hermite error falls as the fourth power of the spacing).  stride
+// > 1 uses every stride-th point only (a coarser start that needs further
+// Newton steps; a diagnostic setting).
+__device__ __forceinline__ void start_T(int i, double target, int stride, double& y, double& lo, double& hi)
 {
-    const double target = ln_ratio - c_lnc[i];
-    double G, D;
-    if (c_lnG_lo[i] - target >= 0.0 || c_lnG_hi[i] - target <= 0.0) {
-        const double T = c_lnG_lo[i] - target >= 0.0 ? T_LO : T_HI;
-        pop_G_warp(i, T, G, D, lane);
-        G_out = G;
-        return T;
+    const double* tab = &g_lnG_tab[i][0];
+    const double* dtab = &g_dlnG_tab[i][0];
+    int a = 0, b = (NTAB - 1) / stride;  // tab[a stride] <= target < tab[b stride]
+    while (b - a > 1) {
+        const int mid = (a + b) >> 1;
+        if (__ldg(tab + mid * stride) <= target) a = mid; else b = mid;
     }
-    double y, lo, hi;
-    start_T(i, target, y, lo, hi);
-    for (int it = 0; it < 100; ++it) {
-        const double T = exp(y);
-        pop_G_warp(i, T, G, D, lane);
-        const double f = log(G) - target;
-        if (f < 0.0) lo = y; else hi = y;
-        double y_new = y - f * G / D;
-        if (!(y_new > lo && y_new < hi)) y_new = 0.5 * (lo + hi);
-        if (fabs(y_new - y) <= 1e-13 * fabs(y)) {
-            G_out = G;
-            return T;
-        }
-        y = y_new;
-    }
-    const double T = exp(y);
-    pop_G_warp(i, T, G, D, lane);
-    G_out = G;
-    return T;
+    const double dy = (log(T_HI) - log(T_LO)) / (NTAB - 1) * stride;
+    lo = log(T_LO) + a * dy;
+    hi = lo + dy;
+    a *= stride;
+    b *= stride;
+    const double ga = __ldg(tab + a), gb = __ldg(tab + b);
+    const double h = gb - ga, u = (target - ga) / h;
+    const double sa = 1.0 / __ldg(dtab + a), sb = 1.0 / __ldg(dtab + b);
+    const double u2 = u * u, u3 = u2 * u;
+    y = (2.0 * u3 - 3.0 * u2 + 1.0) * lo + (u3 - 2.0 * u2 + u) * h * sa + (3.0 * u2 - 2.0 * u3) * hi +
+        (u3 - u2) * h * sb;
+    if (!(y > lo && y < hi)) y = 0.5 * (lo + hi);
 }
 
-__global__ void exact_warp_kernel(const double* __restrict__ A, int n_in, const double* __restrict__ w,
-                                  const double* __restrict__ A2, int n2, const double* __restrict__ w2,
-                                  const float* __restrict__ mass, const unsigned* __restrict__ rows,
-                                  long long nrows, double* __restrict__ emission, float* __restrict__ temperature)
+// Exact emission for rows m = rows ? rows[k] : k, k < nrows, one warp per
+// row.  A second absorbed table A2 [ncell][n2] with its shares w2 (may be
+// NULL) adds its power to each population's.
+//
+// Per population i (on lane i, the three in parallel): P_i = sum_j w_ij A_j,
+// target ln G_i(T_i) = ln(P_i / M) - ln c_i; T_i clamped to 3 or 2000 K when
+// the target lies outside ln G_i over that range, else the table start.
+// Every slot is evaluated at its population's T_i, G_i and T dG_i/dT reduced
+// over the warp; a Newton step on ln T below 1e-13 relative accepts T_i (G_i
+// is then the value at the accepted point, so the row sums to P_i exactly),
+// else Newton / bisection inside the bracket continues for that population and
+// its slots are evaluated again at the final T_i.  Output e_l = sum_i (P_i /
+// G_i) t_il, summed in population order.
+__global__ void __launch_bounds__(32 * EX_WARPS) exact_kernel(
+    const double* __restrict__ A, int n_in, const double* __restrict__ w, const double* __restrict__ A2, int n2,
+    const double* __restrict__ w2, const float* __restrict__ mass, const unsigned* __restrict__ rows, long long nrows,
+    double* __restrict__ emission, float* __restrict__ temperature, int stride)
 {
-    const int lane = threadIdx.x & 31;
-    for (long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nrows;
-         k += ((long long)gridDim.x * blockDim.x) >> 5) {
+    __shared__ double s_a[NS], s_K[NS];       // a_l and K_il by slot
+    __shared__ double s_out[EX_WARPS][NS];    // the row's scaled terms by slot
+    for (int s = threadIdx.x; s < NS; s += blockDim.x) {
+        s_a[s] = c_a[s % NOUT];
+        s_K[s] = c_K[s / NOUT][s % NOUT];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double* buf = s_out[warp];
+    for (long long k = (long long)blockIdx.x * EX_WARPS + warp; k < nrows; k += (long long)gridDim.x * EX_WARPS) {
         const long long m = rows ? (long long)rows[k] : k;
         const double* row = A + (size_t)m * n_in;
         double p0 = 0.0, p1 = 0.0, p2 = 0.0;
         for (int j = lane; j < n_in; j += 32) {
-            const double a = row[j];
-            p0 += __ldg(w + j) * a;
-            p1 += __ldg(w + n_in + j) * a;
-            p2 += __ldg(w + 2 * n_in + j) * a;
+            const double v = __ldcs(row + j);
+            p0 += __ldg(w + j) * v;
+            p1 += __ldg(w + n_in + j) * v;
+            p2 += __ldg(w + 2 * n_in + j) * v;
         }
         if (A2) {
             const double* row2 = A2 + (size_t)m * n2;
             for (int j = lane; j < n2; j += 32) {
-                const double a = row2[j];
-                p0 += __ldg(w2 + j) * a;
-                p1 += __ldg(w2 + n2 + j) * a;
-                p2 += __ldg(w2 + 2 * n2 + j) * a;
+                const double v = __ldcs(row2 + j);
+                p0 += __ldg(w2 + j) * v;
+                p1 += __ldg(w2 + n2 + j) * v;
+                p2 += __ldg(w2 + 2 * n2 + j) * v;
             }
         }
-        const double P[NPOP] = {warp_sum_bcast(p0), warp_sum_bcast(p1), warp_sum_bcast(p2)};
+        p0 = warp_sum_bcast(p0);
+        p1 = warp_sum_bcast(p1);
+        p2 = warp_sum_bcast(p2);
         const double M = (double)mass[m];
-        double T[NPOP], S[NPOP];
-#pragma unroll
-        for (int i = 0; i < NPOP; ++i) {
-            T[i] = 0.0;
-            S[i] = 0.0;
-            if (P[i] > 0.0 && M > 0.0) T[i] = solve_T_warp(i, log(P[i] / M), lane, S[i]);
+        // lane i < NPOP: population i's kind (0 no power, 1 clamped, 2 Newton), target, start, bracket
+        int kind = 0;
+        double tg = 0.0, y = 0.0, lo = 0.0, hi = 0.0, T = 0.0, invT = 0.0;
+        if (lane < NPOP) {
+            const double P = lane == 0 ? p0 : (lane == 1 ? p1 : p2);
+            if (P > 0.0 && M > 0.0) {
+                tg = log(P / M) - c_lnc[lane];
+                if (c_lnG_lo[lane] - tg >= 0.0) {
+                    kind = 1;
+                    T = T_LO;
+                } else if (c_lnG_hi[lane] - tg <= 0.0) {
+                    kind = 1;
+                    T = T_HI;
+                } else {
+                    kind = 2;
+                    start_T(lane, tg, stride, y, lo, hi);
+                    T = exp(y);
+                }
+                invT = 1.0 / T;
+            }
         }
-        double* out = emission + (size_t)m * NOUT;
-        double invT[NPOP], PS[NPOP];
+        const double iT0 = __shfl_sync(0xffffffffu, invT, 0), iT1 = __shfl_sync(0xffffffffu, invT, 1),
+                     iT2 = __shfl_sync(0xffffffffu, invT, 2);
+        const int on = __ballot_sync(0xffffffffu, kind != 0);
+        // one evaluation of every slot; G_i and T dG_i/dT over the lanes
+        double t[EX_SLOTS];
+        double g0 = 0.0, g1 = 0.0, g2 = 0.0, d0 = 0.0, d1 = 0.0, d2 = 0.0;
 #pragma unroll
-        for (int i = 0; i < NPOP; ++i) {
-            invT[i] = S[i] > 0.0 ? 1.0 / T[i] : 0.0;
-            PS[i] = S[i] > 0.0 ? P[i] / S[i] : 0.0;
+        for (int j = 0; j < EX_SLOTS; ++j) {
+            const int s = lane + 32 * j;
+            const int i = s < NOUT ? 0 : (s < 2 * NOUT ? 1 : 2);
+            double tt = 0.0, dd = 0.0;
+            if (s < NS && ((on >> i) & 1)) slot_term(s_a[s], s_K[s], i == 0 ? iT0 : (i == 1 ? iT1 : iT2), tt, dd);
+            t[j] = tt;
+            // slots 32j .. 32j+31 hold at most two populations: the sums stay in registers
+            if (i == 0) { g0 += tt; d0 += dd; }
+            else if (i == 1) { g1 += tt; d1 += dd; }
+            else { g2 += tt; d2 += dd; }
         }
-        for (int l = lane; l < NOUT; l += 32) {
-            double e = 0.0;
-#pragma unroll
-            for (int i = 0; i < NPOP; ++i) {
-                if (S[i] > 0.0) {
-                    const double x = c_a[l] * invT[i];
-                    if (x <= 700.0) e += PS[i] * (c_K[i][l] * (1.0 / expm1(x)));
+        g0 = warp_sum_bcast(g0);
+        g1 = warp_sum_bcast(g1);
+        g2 = warp_sum_bcast(g2);
+        d0 = warp_sum_bcast(d0);
+        d1 = warp_sum_bcast(d1);
+        d2 = warp_sum_bcast(d2);
+        // lane i: the Newton test of population i
+        double G = lane == 0 ? g0 : (lane == 1 ? g1 : g2);
+        bool redo = false;
+        if (lane < NPOP && kind == 2) {
+            const double D = lane == 0 ? d0 : (lane == 1 ? d1 : d2);
+            const double f = log(G) - tg;
+            if (f < 0.0) lo = y; else hi = y;
+            double y_new = y - f * G / D;
+            if (!(y_new > lo && y_new < hi)) y_new = 0.5 * (lo + hi);
+            if (!(fabs(y_new - y) <= 1e-13 * fabs(y))) {
+                redo = true;
+                y = y_new;
+            }
+        }
+        unsigned redo_mask = __ballot_sync(0xffffffffu, redo);
+        while (redo_mask) {  // rare: Newton continues for population i over the whole warp
+            const int i = __ffs(redo_mask) - 1;
+            redo_mask &= redo_mask - 1;
+            double yi = __shfl_sync(0xffffffffu, y, i), loi = __shfl_sync(0xffffffffu, lo, i),
+                   hii = __shfl_sync(0xffffffffu, hi, i);
+            const double tgi = __shfl_sync(0xffffffffu, tg, i);
+            double Ti = exp(yi), Gi = 0.0, Di = 0.0;
+            for (int it = 1; it < 100; ++it) {
+                Ti = exp(yi);
+                pop_G_warp(i, Ti, Gi, Di, lane, s_a, s_K);
+                const double f = log(Gi) - tgi;
+                if (f < 0.0) loi = yi; else hii = yi;
+                double y_new = yi - f * Gi / Di;
+                if (!(y_new > loi && y_new < hii)) y_new = 0.5 * (loi + hii);
+                if (fabs(y_new - yi) <= 1e-13 * fabs(yi)) break;
+                yi = y_new;
+                if (it == 99) {  // iteration limit: the last point's value
+                    Ti = exp(yi);
+                    pop_G_warp(i, Ti, Gi, Di, lane, s_a, s_K);
                 }
             }
-            out[l] = e;
+            if (lane == i) {
+                T = Ti;
+                G = Gi;
+            }
+            const double iTi = 1.0 / Ti;
+#pragma unroll
+            for (int j = 0; j < EX_SLOTS; ++j) {
+                const int s = lane + 32 * j;
+                const int si = s < NOUT ? 0 : (s < 2 * NOUT ? 1 : 2);
+                if (s < NS && si == i) {
+                    double dd;
+                    slot_term(s_a[s], s_K[s], iTi, t[j], dd);
+                }
+            }
         }
-        if (temperature && lane == 0)
-            for (int i = 0; i < NPOP; ++i) temperature[(size_t)m * NPOP + i] = (float)T[i];
+        // output: (P_i / G_i) t_il by slot, then e_l = sum over the populations in order
+        double PS = 0.0;
+        if (lane < NPOP && kind != 0 && G > 0.0) PS = (lane == 0 ? p0 : (lane == 1 ? p1 : p2)) / G;
+        const double PS0 = __shfl_sync(0xffffffffu, PS, 0), PS1 = __shfl_sync(0xffffffffu, PS, 1),
+                     PS2 = __shfl_sync(0xffffffffu, PS, 2);
+#pragma unroll
+        for (int j = 0; j < EX_SLOTS; ++j) {
+            const int s = lane + 32 * j;
+            const int i = s < NOUT ? 0 : (s < 2 * NOUT ? 1 : 2);
+            if (s < NS) buf[s] = (i == 0 ? PS0 : (i == 1 ? PS1 : PS2)) * t[j];
+        }
+        __syncwarp();
+        double* out = emission + (size_t)m * NOUT;
+        for (int l = lane; l < NOUT; l += 32) __stcs(out + l, buf[l] + buf[NOUT + l] + buf[2 * NOUT + l]);
+        if (temperature && lane < NPOP) temperature[(size_t)m * NPOP + lane] = (float)T;
+        __syncwarp();
     }
 }
 
@@ -556,16 +555,21 @@ int launch_exact_emission(const double* absorbed, int n_in, const double* w_dev,
                           cudaStream_t s, const double* absorbed2, int n2, const double* w2_dev)
 {
     ECK(upload_model(s));
-    // a row list (the surrogate's fallback rows): one warp per row.  The FP64
-    // work per row is the same as with a thread per row, spread over the lanes,
-    // and a list of ~1e5 rows then still gives every SM enough warps to keep
-    // its FP64 pipe busy (a thread per row would leave ~20 warps per SM)
-    if (rows && nrows > 0)
-        exact_warp_kernel<<<(int)((nrows + 3) / 4), 128, 0, s>>>(absorbed, n_in, w_dev, absorbed2, n2, w2_dev, mass,
-                                                                rows, nrows, emission, temperature);
-    else if (nrows > 0)
-        exact_kernel<<<grid_blocks(nrows, 128), 128, 0, s>>>(absorbed, n_in, w_dev, absorbed2, n2, w2_dev, mass, rows,
-                                                             nrows, emission, temperature);
+    // one warp per row, every row list alike (all cells, or the surrogate's
+    // fallback rows).  SKIRT_EXACT_TABLE_STRIDE (a power of two up to 64)
+    // starts the Newton solves from a coarser table: the same results through
+    // more Newton steps, a diagnostic of that path.
+    int stride = 1;
+    if (const char* e = std::getenv("SKIRT_EXACT_TABLE_STRIDE")) {
+        const int v = std::atoi(e);
+        if (v >= 1 && v <= 64 && (v & (v - 1)) == 0) stride = v;
+    }
+    if (nrows > 0) {
+        long long blocks = (nrows + EX_WARPS - 1) / EX_WARPS;
+        if (blocks > 152LL * 32) blocks = 152LL * 32;
+        exact_kernel<<<(int)blocks, 32 * EX_WARPS, 0, s>>>(absorbed, n_in, w_dev, absorbed2, n2, w2_dev, mass, rows,
+                                                           nrows, emission, temperature, stride);
+    }
     ECK(cudaGetLastError());
     return SKIRT_OK;
 }

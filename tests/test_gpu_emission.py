@@ -187,6 +187,11 @@ def test_training_reaches_two_percent_and_fallback_is_exact(S):
     assert st2["n_fallback"] == 50
     ref2, _, _ = E.exact_emission(a2, lam, m[n_train:n_train + 50].astype(np.float64))
     np.testing.assert_allclose(em2.cpu().numpy(), ref2, rtol=1e-9, atol=1e-12 * ref2.max())
+    # the fallback rows go through the exact solver's own per-row arithmetic: bit-identical rows
+    ex2 = torch.zeros((50, 100), dtype=torch.float64, device="cuda")
+    S.skirt_dust_emission(_dev(a2, torch.float64), 50, lam.size, lam, md[n_train:n_train + 50].contiguous(),
+                          S.EMIT_EXACT, None, ex2)
+    assert torch.equal(em2, ex2)
     # the guard: the 99th percentile of the training rows' dominant-band share
     share_tr = E.dominant_share(feat[:n_train].cpu().numpy())
     k = int(0.99 * (n_train - 1))
@@ -220,3 +225,32 @@ def test_band_features_and_exact_edges(S, n_in):
     big = ref > 1e-9 * ref.sum(axis=1, keepdims=True)
     np.testing.assert_allclose(g[big], ref[big], rtol=1e-9)
     assert np.all(g[5] == 0)
+
+
+@pytest.mark.parametrize("stride", [32, 64])
+def test_exact_emission_from_a_coarse_start(S, fields, stride, monkeypatch):
+    """The Newton solve started from every stride-th point of the temperature
+    table (a start ~1e-8 from the root, so most populations take more Newton
+    steps than the first evaluation) reaches the same rows: the oracle at
+    1e-9, and the full table's rows to 1e-10 (both accept a point whose Newton
+    step is below 1e-13 of ln T, and a term's relative change is x = a_l/T
+    times the change of ln T, below ~50 for the terms above 1e-9 of the row)."""
+    import torch
+    lam, a, m = fields
+    n = a.shape[0]
+    rows = {}
+    for st in (1, stride):
+        monkeypatch.setenv("SKIRT_EXACT_TABLE_STRIDE", str(st))
+        em = torch.zeros((n, 100), dtype=torch.float64, device="cuda")
+        T = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+        S.skirt_dust_emission(_dev(a, torch.float64), n, lam.size, lam, _dev(m, torch.float32), S.EMIT_EXACT,
+                              None, em, T)
+        rows[st] = (em.cpu().numpy(), T.cpu().numpy())
+    ref, Tref, _ = E.exact_emission(a, lam, m.astype(np.float64))
+    g, T = rows[stride]
+    big = ref > 1e-9 * ref.sum(axis=1, keepdims=True)
+    np.testing.assert_allclose(g[big], ref[big], rtol=1e-9)
+    np.testing.assert_allclose(T, Tref, rtol=1e-6)
+    np.testing.assert_allclose(g[big], rows[1][0][big], rtol=1e-10)
+    good = (m > 0) & (a.sum(axis=1) > 0)
+    np.testing.assert_allclose(g[good].sum(axis=1), a[good].sum(axis=1), rtol=1e-12)
