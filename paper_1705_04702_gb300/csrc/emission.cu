@@ -18,6 +18,7 @@
 #include <mutex>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "skirt_internal.cuh"
 
 namespace skirt {
@@ -44,12 +45,22 @@ __constant__ double c_beta[NPOP];
 constexpr int NTAB = 4097;
 __device__ double g_lnG_tab[NPOP][NTAB];
 __device__ double g_dlnG_tab[NPOP][NTAB];
+// (a_l, K_il) of slot s = i * NOUT + l as double-float pairs (the exact solve's terms)
+__device__ float4 g_slot[NPOP * NOUT];
 
 struct HostModel {
     double lam[NOUT], W[NOUT], a[NOUT], K[NPOP][NOUT];
     double lnc[NPOP], lnG_lo[NPOP], lnG_hi[NPOP];
     double tab[NPOP][NTAB], dtab[NPOP][NTAB];
+    float slot[NPOP * NOUT][4];  // (a_l, K_il) of slot i * NOUT + l as double-float pairs
 };
+
+// v = hi + lo with hi = v rounded to binary32, lo = the rest rounded
+void split_float(double v, float& hi, float& lo)
+{
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
 
 double host_G(const HostModel& h, int i, double T)
 {
@@ -91,6 +102,12 @@ const HostModel& host_model()
                 h.dtab[i][k] = d / g;
             }
         }
+        for (int i = 0; i < NPOP; ++i)
+            for (int l = 0; l < NOUT; ++l) {
+                float* q = h.slot[i * NOUT + l];
+                split_float(h.a[l], q[0], q[1]);
+                split_float(h.K[i][l], q[2], q[3]);
+            }
         ready = true;
     }
     return h;
@@ -107,6 +124,7 @@ cudaError_t upload_model(cudaStream_t s)
     if ((e = cudaMemcpyToSymbolAsync(c_lnG_hi, h.lnG_hi, sizeof h.lnG_hi, 0, cudaMemcpyHostToDevice, s))) return e;
     if ((e = cudaMemcpyToSymbolAsync(g_lnG_tab, h.tab, sizeof h.tab, 0, cudaMemcpyHostToDevice, s))) return e;
     if ((e = cudaMemcpyToSymbolAsync(g_dlnG_tab, h.dtab, sizeof h.dtab, 0, cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyToSymbolAsync(g_slot, h.slot, sizeof h.slot, 0, cudaMemcpyHostToDevice, s))) return e;
     return cudaMemcpyToSymbolAsync(c_beta, BETA, sizeof BETA, 0, cudaMemcpyHostToDevice, s);
 }
 
@@ -208,18 +226,36 @@ int band_blocks(long long ncell)
     return (int)(b < 1 ? 1 : b);
 }
 
-// The exact solve runs one warp per row.  The three populations' terms
-// K_il / expm1(a_l / T_i) form NPOP * NOUT = 300 slots s = i * NOUT + l; lane
-// j holds slots lane + 32 k (k < EX_SLOTS) in registers.  A row costs one
-// evaluation of every population at its starting temperature (the table
-// start below is within a few 1e-14 of the root, so the Newton step there
-// already meets the 1e-13 convergence test), and the output terms are the
-// evaluation's own terms scaled by P_i / G_i: 300 FP64 expm1 per row, against
-// two evaluations per population plus a third pass for the output when the
-// solve starts from a coarse table.
+// The exact solve, one warp per batch of EX_BATCH rows.
+//
+// Per row and population i the solve needs P_i = sum_j w_ij A_j, the target
+// ln G_i(T_i) = ln(P_i / M) - ln c_i, a start and bracket for T_i, one
+// evaluation of G_i(T_i) = sum_l K_il / expm1(a_l / T_i) with T dG_i/dT, and
+// a Newton test; the emission row is e_l = sum_i (P_i / G_i) K_il / expm1(a_l / T_i).
+//
+//  * Per population (FP64, lane 3r + i holds row r's population i, so the
+//    EX_BATCH rows share each FP64 instruction): the target, the clamp to
+//    3 or 2000 K, the table start, T_i, and after the evaluation the Newton
+//    test on ln T.
+//  * Per term (double-float, FP32 pipe; dfloat.cuh): the 300 terms of a row,
+//    slots s = i * NOUT + l, lane j holding slots j + 32 k.  x = a_l / T_i,
+//    expm1(x), its reciprocal, the term t = K_il q and its T dG/dT part
+//    t x (1 + q) (binary32: it only sets the Newton step).  Terms with x > 70
+//    are left out: over 3..2000 K they carry less than 4e-23 of G_i.
+//  * The output row: with E the binary exponent of max_i P_i, the scaled
+//    P_i 2^-E over G_i times each term, summed over the populations in
+//    double-float, widened to FP64 and scaled by 2^E: every row sums to
+//    sum_i P_i to the double-float rounding (~1e-14).
+// The table start is within a few 1e-14 of the root, so the first evaluation
+// passes the 1e-13 convergence test; a population that does not (the coarse-
+// start diagnostic, or a rare target) continues Newton over the whole warp,
+// and its row is evaluated and written again.
 constexpr int NS = NPOP * NOUT;
 constexpr int EX_SLOTS = (NS + 31) / 32;
-constexpr int EX_WARPS = 4;  // warps per block
+constexpr int EX_WARPS = 4;   // warps per block
+constexpr int EX_BATCH = 10;  // rows per warp batch: lanes 3r + i, r < 10
+constexpr float X_CUT = 70.f;
+
 
 __device__ __forceinline__ double warp_sum_bcast(double v)
 {
@@ -228,35 +264,149 @@ __device__ __forceinline__ double warp_sum_bcast(double v)
     return __shfl_sync(0xffffffffu, v, 0);
 }
 
-// term of slot s at 1/T: t = K_il q and its T dG/dT part t x (1 + q), with
-// q = 1 / expm1(x), x = a_l (1/T) (one division per evaluation); a term whose
-// e^x overflows (x > 700) is below 1e-300 of the largest and is left out
-__device__ __forceinline__ void slot_term(double a, double K, double invT, double& t, double& d)
+// binary32 -> FP64 on the integer pipe: exact for normal numbers, zero for
+// zero and subnormals (which the double-float terms only reach below 1e-23
+// of a row)
+__device__ __forceinline__ double widen(float f)
 {
-    t = 0.0;
-    d = 0.0;
-    const double x = a * invT;
-    if (x <= 700.0) {
-        const double q = 1.0 / expm1(x);
-        t = K * q;
-        d = t * x * (1.0 + q);
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xFFu;
+    return e ? __hiloint2double((int)((u & 0x80000000u) | (((u & 0x7FFFFFFFu) >> 3) + 0x38000000u)), (int)(u << 29))
+             : 0.0;
+}
+
+__device__ __forceinline__ double df_to_double(dfl::df2 v) { return widen(v.hi) + widen(v.lo); }
+
+__device__ __forceinline__ dfl::df2 df_from_double(double v)
+{
+    const float h = __double2float_rn(v);
+    return dfl::make(h, __double2float_rn(v - (double)h));
+}
+
+// a / b for b > 0 (double-float): the binary32 quotient and one correction
+__device__ __forceinline__ dfl::df2 df_div(dfl::df2 a, dfl::df2 b)
+{
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    float p, e;
+    dfl::two_prod(b.hi, q1, p, e);
+    float r = __fsub_rn(a.hi, p);  // exact: q1 b.hi is within an ulp of a.hi
+    r = __fsub_rn(r, e);
+    r = __fadd_rn(r, a.lo);
+    r = fmaf(-b.lo, q1, r);
+    return dfl::renorm(q1, __fdiv_rn(r, b.hi));
+}
+
+// term of slot (a, K) at 1/T (double-float): t = K / expm1(a / T), and d =
+// t x (1 + q) in binary32
+__device__ __forceinline__ void slot_term(float4 aK, dfl::df2 invT, dfl::df2& t, float& d)
+{
+    const dfl::df2 x = dfl::mul(dfl::make(aK.x, aK.y), invT);
+    t = dfl::make(0.f, 0.f);
+    d = 0.f;
+    if (x.hi <= X_CUT) {
+        const dfl::df2 q = dfl::recip(dfl::expm1(x));
+        t = dfl::mul(dfl::make(aK.z, aK.w), q);
+        d = t.hi * x.hi * (1.f + q.hi);
     }
 }
 
-// G_i and T dG_i/dT at T for one population, the lanes splitting the
-// wavelengths (the rare Newton solve that needs more than one evaluation)
-__device__ void pop_G_warp(int i, double T, double& G, double& D, int lane, const double* sa, const double* sK)
+__device__ __forceinline__ void warp_sum_df(dfl::df2& v)
 {
-    double g = 0.0, d = 0.0;
-    const double invT = 1.0 / T;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const dfl::df2 w = dfl::make(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+        v = dfl::add(v, w);  // add(a, b) == add(b, a) bit for bit: every lane ends with the same sum
+    }
+}
+
+__device__ __forceinline__ float warp_sum_f(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One row: every slot at its population's 1/T (populations with on bit i),
+// G_i (double-float) and T dG_i/dT (binary32) over the warp, and the output
+// row written from the same terms with the scaled powers Pp_i (P_i 2^-E).
+__device__ __forceinline__ void eval_row(const float4* __restrict__ slot, const dfl::df2 (&iT)[NPOP], unsigned on,
+                                         const dfl::df2 (&Pp)[NPOP], double scale, double* __restrict__ out,
+                                         float2* __restrict__ buf, int lane, dfl::df2 (&G)[NPOP], float (&D)[NPOP])
+{
+    dfl::df2 t[EX_SLOTS];
+    dfl::df2 g[NPOP];
+    float d[NPOP];
+#pragma unroll
+    for (int i = 0; i < NPOP; ++i) {
+        g[i] = dfl::make(0.f, 0.f);
+        d[i] = 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < EX_SLOTS; ++j) {
+        const int s = lane + 32 * j;
+        // slots 32j .. 32j + 31 span at most two populations: i0 for the first
+        // lanes, i1 for the rest (both fixed once the loop is unrolled)
+        const int i0 = (32 * j) / NOUT, i1 = (32 * j + 31) / NOUT < NPOP ? (32 * j + 31) / NOUT : NPOP - 1;
+        const bool first = s < NOUT * (i0 + 1);
+        const int i = first ? i0 : i1;
+        dfl::df2 tt = dfl::make(0.f, 0.f);
+        float dd = 0.f;
+        if (s < NS && ((on >> i) & 1u)) slot_term(slot[s], first ? iT[i0] : iT[i1], tt, dd);
+        t[j] = tt;
+        if (first) {
+            g[i0] = dfl::add(g[i0], tt);
+            d[i0] += dd;
+        } else {
+            g[i1] = dfl::add(g[i1], tt);
+            d[i1] += dd;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NPOP; ++i) {
+        warp_sum_df(g[i]);
+        d[i] = warp_sum_f(d[i]);
+        G[i] = g[i];
+        D[i] = d[i];
+    }
+    dfl::df2 PS[NPOP];
+#pragma unroll
+    for (int i = 0; i < NPOP; ++i)
+        PS[i] = (((on >> i) & 1u) && g[i].hi > 0.f) ? df_div(Pp[i], g[i]) : dfl::make(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < EX_SLOTS; ++j) {
+        const int s = lane + 32 * j;
+        const int i0 = (32 * j) / NOUT, i1 = (32 * j + 31) / NOUT < NPOP ? (32 * j + 31) / NOUT : NPOP - 1;
+        const bool first = s < NOUT * (i0 + 1);
+        if (s < NS) {
+            const dfl::df2 e = dfl::mul(first ? PS[i0] : PS[i1], t[j]);
+            buf[s] = make_float2(e.hi, e.lo);
+        }
+    }
+    __syncwarp();
     for (int l = lane; l < NOUT; l += 32) {
-        double t, dd;
-        slot_term(sa[i * NOUT + l], sK[i * NOUT + l], invT, t, dd);
-        g += t;
+        const float2 b0 = buf[l], b1 = buf[NOUT + l], b2 = buf[2 * NOUT + l];
+        const dfl::df2 e = dfl::add(dfl::add(dfl::make(b0.x, b0.y), dfl::make(b1.x, b1.y)), dfl::make(b2.x, b2.y));
+        __stcs(out + l, df_to_double(e) * scale);
+    }
+    __syncwarp();
+}
+
+// G_i and T dG_i/dT at 1/T for one population, the lanes splitting the
+// wavelengths (the rare Newton solve that needs more than one evaluation)
+__device__ void pop_G_warp(const float4* __restrict__ slot, int i, dfl::df2 iT, int lane, double& G, double& D)
+{
+    dfl::df2 g = dfl::make(0.f, 0.f);
+    float d = 0.f;
+    for (int l = lane; l < NOUT; l += 32) {
+        dfl::df2 t;
+        float dd;
+        slot_term(slot[i * NOUT + l], iT, t, dd);
+        g = dfl::add(g, t);
         d += dd;
     }
-    G = warp_sum_bcast(g);
-    D = warp_sum_bcast(d);
+    warp_sum_df(g);
+    G = df_to_double(g);
+    D = (double)warp_sum_f(d);
 }
 
 // Starting point and bracket of the Newton solve for ln G_i(e^y) = target:
@@ -289,109 +439,109 @@ __device__ __forceinline__ void start_T(int i, double target, int stride, double
     if (!(y > lo && y < hi)) y = 0.5 * (lo + hi);
 }
 
-// Exact emission for rows m = rows ? rows[k] : k, k < nrows, one warp per
-// row.  A second absorbed table A2 [ncell][n2] with its shares w2 (may be
-// NULL) adds its power to each population's.
-//
-// Per population i (on lane i, the three in parallel): P_i = sum_j w_ij A_j,
-// target ln G_i(T_i) = ln(P_i / M) - ln c_i; T_i clamped to 3 or 2000 K when
-// the target lies outside ln G_i over that range, else the table start.
-// Every slot is evaluated at its population's T_i, G_i and T dG_i/dT reduced
-// over the warp; a Newton step on ln T below 1e-13 relative accepts T_i (G_i
-// is then the value at the accepted point, so the row sums to P_i exactly),
-// else Newton / bisection inside the bracket continues for that population and
-// its slots are evaluated again at the final T_i.  Output e_l = sum_i (P_i /
-// G_i) t_il, summed in population order.
+// Exact emission for rows m = rows ? rows[k] : k, k < nrows.  A second
+// absorbed table A2 [ncell][n2] with its shares w2 (may be NULL) adds its
+// power to each population's.
 __global__ void __launch_bounds__(32 * EX_WARPS) exact_kernel(
     const double* __restrict__ A, int n_in, const double* __restrict__ w, const double* __restrict__ A2, int n2,
     const double* __restrict__ w2, const float* __restrict__ mass, const unsigned* __restrict__ rows, long long nrows,
     double* __restrict__ emission, float* __restrict__ temperature, int stride)
 {
-    __shared__ double s_a[NS], s_K[NS];       // a_l and K_il by slot
-    __shared__ double s_out[EX_WARPS][NS];    // the row's scaled terms by slot
-    for (int s = threadIdx.x; s < NS; s += blockDim.x) {
-        s_a[s] = c_a[s % NOUT];
-        s_K[s] = c_K[s / NOUT][s % NOUT];
-    }
+    __shared__ float4 s_slot[NS];
+    __shared__ float2 s_buf[EX_WARPS][NS];
+    for (int s = threadIdx.x; s < NS; s += blockDim.x) s_slot[s] = g_slot[s];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double* buf = s_out[warp];
-    for (long long k = (long long)blockIdx.x * EX_WARPS + warp; k < nrows; k += (long long)gridDim.x * EX_WARPS) {
-        const long long m = rows ? (long long)rows[k] : k;
-        const double* row = A + (size_t)m * n_in;
-        double p0 = 0.0, p1 = 0.0, p2 = 0.0;
-        for (int j = lane; j < n_in; j += 32) {
-            const double v = __ldcs(row + j);
-            p0 += __ldg(w + j) * v;
-            p1 += __ldg(w + n_in + j) * v;
-            p2 += __ldg(w + 2 * n_in + j) * v;
-        }
-        if (A2) {
-            const double* row2 = A2 + (size_t)m * n2;
-            for (int j = lane; j < n2; j += 32) {
-                const double v = __ldcs(row2 + j);
-                p0 += __ldg(w2 + j) * v;
-                p1 += __ldg(w2 + n2 + j) * v;
-                p2 += __ldg(w2 + 2 * n2 + j) * v;
+    float2* buf = s_buf[warp];
+    const int my_r = lane / NPOP, my_i = lane - NPOP * (lane / NPOP);  // this lane's (row, population)
+    for (long long base = ((long long)blockIdx.x * EX_WARPS + warp) * EX_BATCH; base < nrows;
+         base += (long long)gridDim.x * EX_WARPS * EX_BATCH) {
+        const int nb = nrows - base < EX_BATCH ? (int)(nrows - base) : EX_BATCH;
+        const bool mine = my_r < nb;
+        const long long my_m = mine ? (rows ? (long long)rows[base + my_r] : base + my_r) : 0;
+        // ---- population powers, one row at a time over the lanes (FP64)
+        double P = 0.0;
+        int E = 0;
+        for (int r = 0; r < nb; ++r) {
+            const long long m = rows ? (long long)rows[base + r] : base + r;
+            const double* row = A + (size_t)m * n_in;
+            double p0 = 0.0, p1 = 0.0, p2 = 0.0;
+            for (int j = lane; j < n_in; j += 32) {
+                const double v = __ldcs(row + j);
+                p0 += __ldg(w + j) * v;
+                p1 += __ldg(w + n_in + j) * v;
+                p2 += __ldg(w + 2 * n_in + j) * v;
             }
-        }
-        p0 = warp_sum_bcast(p0);
-        p1 = warp_sum_bcast(p1);
-        p2 = warp_sum_bcast(p2);
-        const double M = (double)mass[m];
-        // lane i < NPOP: population i's kind (0 no power, 1 clamped, 2 Newton), target, start, bracket
-        int kind = 0;
-        double tg = 0.0, y = 0.0, lo = 0.0, hi = 0.0, T = 0.0, invT = 0.0;
-        if (lane < NPOP) {
-            const double P = lane == 0 ? p0 : (lane == 1 ? p1 : p2);
-            if (P > 0.0 && M > 0.0) {
-                tg = log(P / M) - c_lnc[lane];
-                if (c_lnG_lo[lane] - tg >= 0.0) {
-                    kind = 1;
-                    T = T_LO;
-                } else if (c_lnG_hi[lane] - tg <= 0.0) {
-                    kind = 1;
-                    T = T_HI;
-                } else {
-                    kind = 2;
-                    start_T(lane, tg, stride, y, lo, hi);
-                    T = exp(y);
+            if (A2) {
+                const double* row2 = A2 + (size_t)m * n2;
+                for (int j = lane; j < n2; j += 32) {
+                    const double v = __ldcs(row2 + j);
+                    p0 += __ldg(w2 + j) * v;
+                    p1 += __ldg(w2 + n2 + j) * v;
+                    p2 += __ldg(w2 + 2 * n2 + j) * v;
                 }
-                invT = 1.0 / T;
+            }
+            p0 = warp_sum_bcast(p0);
+            p1 = warp_sum_bcast(p1);
+            p2 = warp_sum_bcast(p2);
+            if (my_r == r) {
+                P = my_i == 0 ? p0 : (my_i == 1 ? p1 : p2);
+                // binary exponent of the row's largest population power (0 if none is positive)
+                const double pm = fmax(fmax(p0, p1), p2);
+                E = pm > 0.0 ? ((__double2hiint(pm) >> 20) & 0x7FF) - 1023 : 0;
+                E = E < -1000 ? -1000 : (E > 1000 ? 1000 : E);
             }
         }
-        const double iT0 = __shfl_sync(0xffffffffu, invT, 0), iT1 = __shfl_sync(0xffffffffu, invT, 1),
-                     iT2 = __shfl_sync(0xffffffffu, invT, 2);
-        const int on = __ballot_sync(0xffffffffu, kind != 0);
-        // one evaluation of every slot; G_i and T dG_i/dT over the lanes
-        double t[EX_SLOTS];
-        double g0 = 0.0, g1 = 0.0, g2 = 0.0, d0 = 0.0, d1 = 0.0, d2 = 0.0;
-#pragma unroll
-        for (int j = 0; j < EX_SLOTS; ++j) {
-            const int s = lane + 32 * j;
-            const int i = s < NOUT ? 0 : (s < 2 * NOUT ? 1 : 2);
-            double tt = 0.0, dd = 0.0;
-            if (s < NS && ((on >> i) & 1)) slot_term(s_a[s], s_K[s], i == 0 ? iT0 : (i == 1 ? iT1 : iT2), tt, dd);
-            t[j] = tt;
-            // slots 32j .. 32j+31 hold at most two populations: the sums stay in registers
-            if (i == 0) { g0 += tt; d0 += dd; }
-            else if (i == 1) { g1 += tt; d1 += dd; }
-            else { g2 += tt; d2 += dd; }
+        // ---- per population (FP64): target, clamp or table start, 1/T, scaled power
+        const float M = mine ? mass[my_m] : 0.f;
+        int kind = 0;  // 0 no power, 1 clamped, 2 Newton
+        double tg = 0.0, y = 0.0, lo = 0.0, hi = 0.0, T = 0.0;
+        dfl::df2 iT = dfl::make(0.f, 0.f), Pp = dfl::make(0.f, 0.f);
+        if (mine && P > 0.0 && M > 0.f) {
+            tg = log(P / (double)M) - c_lnc[my_i];
+            if (c_lnG_lo[my_i] - tg >= 0.0) {
+                kind = 1;
+                T = T_LO;
+            } else if (c_lnG_hi[my_i] - tg <= 0.0) {
+                kind = 1;
+                T = T_HI;
+            } else {
+                kind = 2;
+                start_T(my_i, tg, stride, y, lo, hi);
+                T = exp(y);
+            }
+            iT = df_from_double(1.0 / T);
+            Pp = df_from_double(P * __longlong_as_double((long long)(1023 - E) << 52));
         }
-        g0 = warp_sum_bcast(g0);
-        g1 = warp_sum_bcast(g1);
-        g2 = warp_sum_bcast(g2);
-        d0 = warp_sum_bcast(d0);
-        d1 = warp_sum_bcast(d1);
-        d2 = warp_sum_bcast(d2);
-        // lane i: the Newton test of population i
-        double G = lane == 0 ? g0 : (lane == 1 ? g1 : g2);
+        const unsigned on_all = __ballot_sync(0xffffffffu, kind != 0);
+        // ---- one evaluation per row (double-float); lane 3r + i keeps its G_i, D_i
+        dfl::df2 Gm = dfl::make(0.f, 0.f);
+        float Dm = 0.f;
+        for (int r = 0; r < nb; ++r) {
+            const int l0 = NPOP * r;
+            dfl::df2 iTr[NPOP], Ppr[NPOP], G[NPOP];
+            float D[NPOP];
+#pragma unroll
+            for (int i = 0; i < NPOP; ++i) {
+                iTr[i] = dfl::make(__shfl_sync(0xffffffffu, iT.hi, l0 + i), __shfl_sync(0xffffffffu, iT.lo, l0 + i));
+                Ppr[i] = dfl::make(__shfl_sync(0xffffffffu, Pp.hi, l0 + i), __shfl_sync(0xffffffffu, Pp.lo, l0 + i));
+            }
+            const int Er = __shfl_sync(0xffffffffu, E, l0);
+            const long long m = rows ? (long long)rows[base + r] : base + r;
+            eval_row(s_slot, iTr, (on_all >> l0) & 7u, Ppr, __longlong_as_double((long long)(Er + 1023) << 52),
+                     emission + (size_t)m * NOUT, buf, lane, G, D);
+            if (my_r == r) {
+                Gm = my_i == 0 ? G[0] : (my_i == 1 ? G[1] : G[2]);
+                Dm = my_i == 0 ? D[0] : (my_i == 1 ? D[1] : D[2]);
+            }
+        }
+        // ---- Newton test of every population (FP64)
         bool redo = false;
-        if (lane < NPOP && kind == 2) {
-            const double D = lane == 0 ? d0 : (lane == 1 ? d1 : d2);
+        if (kind == 2) {
+            const double G = df_to_double(Gm);
             const double f = log(G) - tg;
             if (f < 0.0) lo = y; else hi = y;
-            double y_new = y - f * G / D;
+            double y_new = y - f * G / (double)Dm;
             if (!(y_new > lo && y_new < hi)) y_new = 0.5 * (lo + hi);
             if (!(fabs(y_new - y) <= 1e-13 * fabs(y))) {
                 redo = true;
@@ -399,58 +549,44 @@ __global__ void __launch_bounds__(32 * EX_WARPS) exact_kernel(
             }
         }
         unsigned redo_mask = __ballot_sync(0xffffffffu, redo);
-        while (redo_mask) {  // rare: Newton continues for population i over the whole warp
-            const int i = __ffs(redo_mask) - 1;
+        while (redo_mask) {  // rare: Newton continues for one population over the whole warp
+            const int L = __ffs(redo_mask) - 1;
             redo_mask &= redo_mask - 1;
-            double yi = __shfl_sync(0xffffffffu, y, i), loi = __shfl_sync(0xffffffffu, lo, i),
-                   hii = __shfl_sync(0xffffffffu, hi, i);
-            const double tgi = __shfl_sync(0xffffffffu, tg, i);
+            const int ri = L / NPOP, ii = L - NPOP * ri;
+            double yi = __shfl_sync(0xffffffffu, y, L), loi = __shfl_sync(0xffffffffu, lo, L),
+                   hii = __shfl_sync(0xffffffffu, hi, L);
+            const double tgi = __shfl_sync(0xffffffffu, tg, L);
             double Ti = exp(yi), Gi = 0.0, Di = 0.0;
             for (int it = 1; it < 100; ++it) {
                 Ti = exp(yi);
-                pop_G_warp(i, Ti, Gi, Di, lane, s_a, s_K);
+                pop_G_warp(s_slot, ii, df_from_double(1.0 / Ti), lane, Gi, Di);
                 const double f = log(Gi) - tgi;
                 if (f < 0.0) loi = yi; else hii = yi;
                 double y_new = yi - f * Gi / Di;
                 if (!(y_new > loi && y_new < hii)) y_new = 0.5 * (loi + hii);
                 if (fabs(y_new - yi) <= 1e-13 * fabs(yi)) break;
                 yi = y_new;
-                if (it == 99) {  // iteration limit: the last point's value
-                    Ti = exp(yi);
-                    pop_G_warp(i, Ti, Gi, Di, lane, s_a, s_K);
-                }
+                if (it == 99) Ti = exp(yi);  // iteration limit: the last point
             }
-            if (lane == i) {
+            if (lane == L) {
                 T = Ti;
-                G = Gi;
+                iT = df_from_double(1.0 / Ti);
             }
-            const double iTi = 1.0 / Ti;
+            // the row again, with the population's final temperature
+            const int l0 = NPOP * ri;
+            dfl::df2 iTr[NPOP], Ppr[NPOP], G[NPOP];
+            float D[NPOP];
 #pragma unroll
-            for (int j = 0; j < EX_SLOTS; ++j) {
-                const int s = lane + 32 * j;
-                const int si = s < NOUT ? 0 : (s < 2 * NOUT ? 1 : 2);
-                if (s < NS && si == i) {
-                    double dd;
-                    slot_term(s_a[s], s_K[s], iTi, t[j], dd);
-                }
+            for (int i = 0; i < NPOP; ++i) {
+                iTr[i] = dfl::make(__shfl_sync(0xffffffffu, iT.hi, l0 + i), __shfl_sync(0xffffffffu, iT.lo, l0 + i));
+                Ppr[i] = dfl::make(__shfl_sync(0xffffffffu, Pp.hi, l0 + i), __shfl_sync(0xffffffffu, Pp.lo, l0 + i));
             }
+            const int Er = __shfl_sync(0xffffffffu, E, l0);
+            const long long m = rows ? (long long)rows[base + ri] : base + ri;
+            eval_row(s_slot, iTr, (on_all >> l0) & 7u, Ppr, __longlong_as_double((long long)(Er + 1023) << 52),
+                     emission + (size_t)m * NOUT, buf, lane, G, D);
         }
-        // output: (P_i / G_i) t_il by slot, then e_l = sum over the populations in order
-        double PS = 0.0;
-        if (lane < NPOP && kind != 0 && G > 0.0) PS = (lane == 0 ? p0 : (lane == 1 ? p1 : p2)) / G;
-        const double PS0 = __shfl_sync(0xffffffffu, PS, 0), PS1 = __shfl_sync(0xffffffffu, PS, 1),
-                     PS2 = __shfl_sync(0xffffffffu, PS, 2);
-#pragma unroll
-        for (int j = 0; j < EX_SLOTS; ++j) {
-            const int s = lane + 32 * j;
-            const int i = s < NOUT ? 0 : (s < 2 * NOUT ? 1 : 2);
-            if (s < NS) buf[s] = (i == 0 ? PS0 : (i == 1 ? PS1 : PS2)) * t[j];
-        }
-        __syncwarp();
-        double* out = emission + (size_t)m * NOUT;
-        for (int l = lane; l < NOUT; l += 32) __stcs(out + l, buf[l] + buf[NOUT + l] + buf[2 * NOUT + l]);
-        if (temperature && lane < NPOP) temperature[(size_t)m * NPOP + lane] = (float)T;
-        __syncwarp();
+        if (temperature && mine) temperature[(size_t)my_m * NPOP + my_i] = (float)T;
     }
 }
 
@@ -555,8 +691,8 @@ int launch_exact_emission(const double* absorbed, int n_in, const double* w_dev,
                           cudaStream_t s, const double* absorbed2, int n2, const double* w2_dev)
 {
     ECK(upload_model(s));
-    // one warp per row, every row list alike (all cells, or the surrogate's
-    // fallback rows).  SKIRT_EXACT_TABLE_STRIDE (a power of two up to 64)
+    // one warp per batch of rows, every row list alike (all cells, or the
+    // surrogate's fallback rows).  SKIRT_EXACT_TABLE_STRIDE (a power of two up to 64)
     // starts the Newton solves from a coarser table: the same results through
     // more Newton steps, a diagnostic of that path.
     int stride = 1;
@@ -565,7 +701,7 @@ int launch_exact_emission(const double* absorbed, int n_in, const double* w_dev,
         if (v >= 1 && v <= 64 && (v & (v - 1)) == 0) stride = v;
     }
     if (nrows > 0) {
-        long long blocks = (nrows + EX_WARPS - 1) / EX_WARPS;
+        long long blocks = (nrows + EX_WARPS * EX_BATCH - 1) / (EX_WARPS * EX_BATCH);
         if (blocks > 152LL * 32) blocks = 152LL * 32;
         exact_kernel<<<(int)blocks, 32 * EX_WARPS, 0, s>>>(absorbed, n_in, w_dev, absorbed2, n2, w2_dev, mass, rows,
                                                            nrows, emission, temperature, stride);
