@@ -296,18 +296,24 @@ __device__ __forceinline__ dfl::df2 df_div(dfl::df2 a, dfl::df2 b)
     return dfl::renorm(q1, __fdiv_rn(r, b.hi));
 }
 
+struct TermOut {
+    float th, tl, d;
+};
+
 // term of slot (a, K) at 1/T (double-float): t = K / expm1(a / T), and d =
-// t x (1 + q) in binary32
-__device__ __forceinline__ void slot_term(float4 aK, dfl::df2 invT, dfl::df2& t, float& d)
+// t x (1 + q) in binary32 (one copy of the code for every caller)
+__device__ __noinline__ TermOut slot_term(float4 aK, float ih, float il)
 {
-    const dfl::df2 x = dfl::mul(dfl::make(aK.x, aK.y), invT);
-    t = dfl::make(0.f, 0.f);
-    d = 0.f;
+    const dfl::df2 x = dfl::mul(dfl::make(aK.x, aK.y), dfl::make(ih, il));
+    TermOut o = {0.f, 0.f, 0.f};
     if (x.hi <= X_CUT) {
         const dfl::df2 q = dfl::recip(dfl::expm1(x));
-        t = dfl::mul(dfl::make(aK.z, aK.w), q);
-        d = t.hi * x.hi * (1.f + q.hi);
+        const dfl::df2 t = dfl::mul(dfl::make(aK.z, aK.w), q);
+        o.th = t.hi;
+        o.tl = t.lo;
+        o.d = t.hi * x.hi * (1.f + q.hi);
     }
+    return o;
 }
 
 __device__ __forceinline__ void warp_sum_df(dfl::df2& v)
@@ -328,64 +334,43 @@ __device__ __forceinline__ float warp_sum_f(float v)
 
 // One row: every slot at its population's 1/T (populations with on bit i),
 // G_i (double-float) and T dG_i/dT (binary32) over the warp, and the output
-// row written from the same terms with the scaled powers Pp_i (P_i 2^-E).
+// row written from the same terms (staged in buf) with the scaled powers
+// Pp_i (P_i 2^-E).  The slot loop is not unrolled and the term is one
+// non-inlined routine: unrolled, the solve's code outgrew the instruction
+// cache and the warps stalled on instruction fetch.
 __device__ __forceinline__ void eval_row(const float4* __restrict__ slot, const dfl::df2 (&iT)[NPOP], unsigned on,
                                          const dfl::df2 (&Pp)[NPOP], double scale, double* __restrict__ out,
                                          float2* __restrict__ buf, int lane, dfl::df2 (&G)[NPOP], float (&D)[NPOP])
 {
-    dfl::df2 t[EX_SLOTS];
-    dfl::df2 g[NPOP];
-    float d[NPOP];
-#pragma unroll
-    for (int i = 0; i < NPOP; ++i) {
-        g[i] = dfl::make(0.f, 0.f);
-        d[i] = 0.f;
-    }
-#pragma unroll
+    dfl::df2 g0 = dfl::make(0.f, 0.f), g1 = g0, g2 = g0;
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+#pragma unroll 1
     for (int j = 0; j < EX_SLOTS; ++j) {
         const int s = lane + 32 * j;
-        // slots 32j .. 32j + 31 span at most two populations: i0 for the first
-        // lanes, i1 for the rest (both fixed once the loop is unrolled)
-        const int i0 = (32 * j) / NOUT, i1 = (32 * j + 31) / NOUT < NPOP ? (32 * j + 31) / NOUT : NPOP - 1;
-        const bool first = s < NOUT * (i0 + 1);
-        const int i = first ? i0 : i1;
-        dfl::df2 tt = dfl::make(0.f, 0.f);
-        float dd = 0.f;
-        if (s < NS && ((on >> i) & 1u)) slot_term(slot[s], first ? iT[i0] : iT[i1], tt, dd);
-        t[j] = tt;
-        if (first) {
-            g[i0] = dfl::add(g[i0], tt);
-            d[i0] += dd;
-        } else {
-            g[i1] = dfl::add(g[i1], tt);
-            d[i1] += dd;
+        const int i = s < NOUT ? 0 : (s < 2 * NOUT ? 1 : 2);
+        TermOut o = {0.f, 0.f, 0.f};
+        if (s < NS && ((on >> i) & 1u)) {
+            const dfl::df2 it = i == 0 ? iT[0] : (i == 1 ? iT[1] : iT[2]);
+            o = slot_term(slot[s], it.hi, it.lo);
         }
+        if (s < NS) buf[s] = make_float2(o.th, o.tl);
+        const dfl::df2 tt = dfl::make(o.th, o.tl);
+        if (i == 0) { g0 = dfl::add(g0, tt); d0 += o.d; }
+        else if (i == 1) { g1 = dfl::add(g1, tt); d1 += o.d; }
+        else { g2 = dfl::add(g2, tt); d2 += o.d; }
     }
-#pragma unroll
-    for (int i = 0; i < NPOP; ++i) {
-        warp_sum_df(g[i]);
-        d[i] = warp_sum_f(d[i]);
-        G[i] = g[i];
-        D[i] = d[i];
-    }
+    warp_sum_df(g0); warp_sum_df(g1); warp_sum_df(g2);
+    G[0] = g0; G[1] = g1; G[2] = g2;
+    D[0] = warp_sum_f(d0); D[1] = warp_sum_f(d1); D[2] = warp_sum_f(d2);
     dfl::df2 PS[NPOP];
 #pragma unroll
     for (int i = 0; i < NPOP; ++i)
-        PS[i] = (((on >> i) & 1u) && g[i].hi > 0.f) ? df_div(Pp[i], g[i]) : dfl::make(0.f, 0.f);
-#pragma unroll
-    for (int j = 0; j < EX_SLOTS; ++j) {
-        const int s = lane + 32 * j;
-        const int i0 = (32 * j) / NOUT, i1 = (32 * j + 31) / NOUT < NPOP ? (32 * j + 31) / NOUT : NPOP - 1;
-        const bool first = s < NOUT * (i0 + 1);
-        if (s < NS) {
-            const dfl::df2 e = dfl::mul(first ? PS[i0] : PS[i1], t[j]);
-            buf[s] = make_float2(e.hi, e.lo);
-        }
-    }
+        PS[i] = (((on >> i) & 1u) && G[i].hi > 0.f) ? df_div(Pp[i], G[i]) : dfl::make(0.f, 0.f);
     __syncwarp();
     for (int l = lane; l < NOUT; l += 32) {
         const float2 b0 = buf[l], b1 = buf[NOUT + l], b2 = buf[2 * NOUT + l];
-        const dfl::df2 e = dfl::add(dfl::add(dfl::make(b0.x, b0.y), dfl::make(b1.x, b1.y)), dfl::make(b2.x, b2.y));
+        const dfl::df2 e = dfl::add(dfl::add(dfl::mul(PS[0], dfl::make(b0.x, b0.y)), dfl::mul(PS[1], dfl::make(b1.x, b1.y))),
+                                    dfl::mul(PS[2], dfl::make(b2.x, b2.y)));
         __stcs(out + l, df_to_double(e) * scale);
     }
     __syncwarp();
@@ -398,11 +383,9 @@ __device__ void pop_G_warp(const float4* __restrict__ slot, int i, dfl::df2 iT, 
     dfl::df2 g = dfl::make(0.f, 0.f);
     float d = 0.f;
     for (int l = lane; l < NOUT; l += 32) {
-        dfl::df2 t;
-        float dd;
-        slot_term(slot[i * NOUT + l], iT, t, dd);
-        g = dfl::add(g, t);
-        d += dd;
+        const TermOut o = slot_term(slot[i * NOUT + l], iT.hi, iT.lo);
+        g = dfl::add(g, dfl::make(o.th, o.tl));
+        d += o.d;
     }
     warp_sum_df(g);
     G = df_to_double(g);
@@ -538,12 +521,16 @@ __global__ void __launch_bounds__(32 * EX_WARPS) exact_kernel(
         // ---- Newton test of every population (FP64)
         bool redo = false;
         if (kind == 2) {
+            // converged when the Newton step is below 1e-13 of ln T (tested before the
+            // bracket: a start exact to the last bit gives a zero step, and y itself
+            // then sits on the updated bracket's end)
             const double G = df_to_double(Gm);
             const double f = log(G) - tg;
-            if (f < 0.0) lo = y; else hi = y;
-            double y_new = y - f * G / (double)Dm;
-            if (!(y_new > lo && y_new < hi)) y_new = 0.5 * (lo + hi);
-            if (!(fabs(y_new - y) <= 1e-13 * fabs(y))) {
+            const double step = f * G / (double)Dm;
+            if (!(fabs(step) <= 1e-13 * fabs(y))) {
+                if (f < 0.0) lo = y; else hi = y;
+                double y_new = y - step;
+                if (!(y_new > lo && y_new < hi)) y_new = 0.5 * (lo + hi);
                 redo = true;
                 y = y_new;
             }
@@ -561,10 +548,11 @@ __global__ void __launch_bounds__(32 * EX_WARPS) exact_kernel(
                 Ti = exp(yi);
                 pop_G_warp(s_slot, ii, df_from_double(1.0 / Ti), lane, Gi, Di);
                 const double f = log(Gi) - tgi;
+                const double step = f * Gi / Di;
+                if (fabs(step) <= 1e-13 * fabs(yi)) break;
                 if (f < 0.0) loi = yi; else hii = yi;
-                double y_new = yi - f * Gi / Di;
+                double y_new = yi - step;
                 if (!(y_new > loi && y_new < hii)) y_new = 0.5 * (loi + hii);
-                if (fabs(y_new - yi) <= 1e-13 * fabs(yi)) break;
                 yi = y_new;
                 if (it == 99) Ti = exp(yi);  // iteration limit: the last point
             }
