@@ -254,3 +254,30 @@ def test_exact_emission_from_a_coarse_start(S, fields, stride, monkeypatch):
     np.testing.assert_allclose(g[big], rows[1][0][big], rtol=1e-10)
     good = (m > 0) & (a.sum(axis=1) > 0)
     np.testing.assert_allclose(g[good].sum(axis=1), a[good].sum(axis=1), rtol=1e-12)
+
+
+@pytest.mark.parametrize("scale", [1e-200, 1e-40, 1e40, 1e200])
+def test_exact_emission_at_extreme_powers(S, scale):
+    """Absorbed powers scaled far outside the temperature range: every
+    population clamps at 3 K (small powers) or 2000 K (large ones), and the
+    rows, whose powers the solve carries as a double-float times 2^E, still
+    match the oracle and sum to the absorbed power, down to 1e-200 and up to
+    1e200 of the cells' usual power (the synthetic spectra reach 1e-323, so
+    a smaller scale would leave the rows' powers to subnormal arithmetic,
+    which the host's matrix product may flush)."""
+    import torch
+    lam = np.geomspace(0.09, 10.0, 200)
+    n = 257
+    a, m = W.absorbed_spectra(n, lam, seed=13)
+    a = a * scale
+    em = torch.zeros((n, 100), dtype=torch.float64, device="cuda")
+    T = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    S.skirt_dust_emission(_dev(a, torch.float64), n, lam.size, lam, _dev(m, torch.float32), S.EMIT_EXACT, None,
+                          em, T)
+    ref, Tref, _ = E.exact_emission(a, lam, m.astype(np.float64))
+    assert np.all(Tref == (3.0 if scale < 1 else 2000.0))
+    g = em.cpu().numpy()
+    big = ref > 1e-9 * ref.sum(axis=1, keepdims=True)
+    np.testing.assert_allclose(g[big], ref[big], rtol=1e-9)
+    assert np.array_equal(T.cpu().numpy(), Tref.astype(np.float32))
+    np.testing.assert_allclose(g.sum(axis=1), a.sum(axis=1), rtol=1e-12)
