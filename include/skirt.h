@@ -388,7 +388,10 @@ typedef struct {
  * network's hull or guard (net required).  absorbed: device double[ncell][n_in];
  * lambda_in: host double[n_in]; mass: device float[ncell]; emission: device
  * double[ncell][100]; temperature: device float[ncell][3] or NULL (exact rows
- * only; 0 for surrogate rows); stats: host or NULL. */
+ * only; 0 for surrogate rows); stats: host or NULL.  Surrogate mode keeps its
+ * working tables (~150 bytes per cell) in the network handle, allocated on the
+ * first call that needs them and freed by skirt_mlp_destroy; calls that share
+ * a network run one at a time. */
 int skirt_dust_emission(const double* absorbed, long long ncell, int n_in, const double* lambda_in,
                         const float* mass, int mode, skirt_mlp_t net, double* emission, float* temperature,
                         skirt_emission_stats* stats, void* stream);

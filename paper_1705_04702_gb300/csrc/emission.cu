@@ -772,20 +772,34 @@ extern "C" int skirt_dust_emission(const double* absorbed, long long ncell, int 
         rc = launch_exact_emission(absorbed, n_in, d_w, mass, nullptr, ncell, emission, temperature, s);
         ECK(cudaEventRecord(ev[1], s));
     } else {
-        float* d_feat = nullptr;
-        double* d_tot = nullptr;
-        unsigned char* d_flag = nullptr;
-        unsigned* d_rows = nullptr;
-        unsigned long long* d_cnt = nullptr;
-        ECK(cudaMallocAsync((void**)&d_feat, sizeof(float) * NB * (size_t)ncell, s));
-        ECK(cudaMallocAsync((void**)&d_tot, sizeof(double) * (size_t)ncell, s));
-        ECK(cudaMallocAsync((void**)&d_flag, (size_t)ncell, s));
-        ECK(cudaMallocAsync((void**)&d_rows, sizeof(unsigned) * (size_t)ncell, s));
-        ECK(cudaMallocAsync((void**)&d_cnt, sizeof(unsigned long long), s));
+        // the working tables live in the network's workspace (grown on demand, kept
+        // between calls): a stream-ordered allocation of ~2.5 GB per call cost ~5 ms
+        std::unique_lock<std::mutex> ws_lock(mlp_workspace_mutex(net));
+        // on every way out of this block (errors included) the stream drains
+        // before the lock is released, so no other call reuses tables in use
+        struct DrainOnExit {
+            cudaStream_t s;
+            ~DrainOnExit() { cudaStreamSynchronize(s); }
+        } drain{s};
+        auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+        const size_t o_tot = 0, o_cnt = o_tot + al(sizeof(double) * (size_t)ncell), o_start = o_cnt + al(8),
+                     o_feat = o_start + al(sizeof(int) * (NB + 1)),
+                     o_rows = o_feat + al(sizeof(float) * NB * (size_t)ncell),
+                     o_flag = o_rows + al(sizeof(unsigned) * (size_t)ncell), ws_total = o_flag + al((size_t)ncell);
+        unsigned char* ws = nullptr;
+        if (int r = mlp_workspace(net, ws_total, (void**)&ws)) {
+            cudaFreeAsync(d_w, s);
+            for (auto& e : ev) cudaEventDestroy(e);
+            return r;
+        }
+        double* d_tot = (double*)(ws + o_tot);
+        unsigned long long* d_cnt = (unsigned long long*)(ws + o_cnt);
+        int* d_start = (int*)(ws + o_start);
+        float* d_feat = (float*)(ws + o_feat);
+        unsigned* d_rows = (unsigned*)(ws + o_rows);
+        unsigned char* d_flag = ws + o_flag;
         ECK(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), s));
         std::vector<int> start = band_starts(lambda_in, n_in);
-        int* d_start = nullptr;
-        ECK(cudaMallocAsync((void**)&d_start, sizeof(int) * (NB + 1), s));
         ECK(cudaMemcpyAsync(d_start, start.data(), sizeof(int) * (NB + 1), cudaMemcpyHostToDevice, s));
         if (temperature) zero_temperature_kernel<<<grid_blocks(3 * ncell, 256), 256, 0, s>>>(temperature, 3 * ncell);
         ECK(cudaEventRecord(ev[0], s));
@@ -802,12 +816,6 @@ extern "C" int skirt_dust_emission(const double* absorbed, long long ncell, int 
             rc = launch_exact_emission(absorbed, n_in, d_w, mass, d_rows, (long long)nfb, emission, temperature, s);
             ECK(cudaEventRecord(ev[3], s));
         }
-        cudaFreeAsync(d_feat, s);
-        cudaFreeAsync(d_tot, s);
-        cudaFreeAsync(d_flag, s);
-        cudaFreeAsync(d_rows, s);
-        cudaFreeAsync(d_cnt, s);
-        cudaFreeAsync(d_start, s);
     }
     cudaFreeAsync(d_w, s);
     ECK(cudaStreamSynchronize(s));

@@ -23,6 +23,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "skirt_internal.cuh"
@@ -457,6 +458,12 @@ struct skirt_mlp_s {
     float host_stats[4 * NIN]; // mean, std, lo, hi
     float share_max = 1.f;     // guard: rows whose dominant band holds more of the power go to the exact solver
     bool packed = false;
+    // working tables of skirt_dust_emission's surrogate mode (features, totals,
+    // flags, fallback rows), grown on demand and kept until the network is
+    // destroyed; ws_mu serialises the calls that use them
+    std::mutex ws_mu;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
 };
 
 namespace skirt {
@@ -479,6 +486,22 @@ static int repack(skirt_mlp_s* net, cudaStream_t s)
     pack_inference_kernel<<<64, 256, 0, s>>>(net->P, net->Wb, net->Bb);
     MCK(cudaGetLastError());
     net->packed = true;
+    return SKIRT_OK;
+}
+
+std::mutex& mlp_workspace_mutex(skirt_mlp_s* net) { return net->ws_mu; }
+
+int mlp_workspace(skirt_mlp_s* net, size_t bytes, void** p)
+{
+    if (bytes > net->ws_bytes) {
+        // the previous calls have synchronised their streams: the old tables are idle
+        cudaFree(net->ws);
+        net->ws = nullptr;
+        net->ws_bytes = 0;
+        MCK(cudaMalloc(&net->ws, bytes));
+        net->ws_bytes = bytes;
+    }
+    *p = net->ws;
     return SKIRT_OK;
 }
 
@@ -572,6 +595,7 @@ extern "C" int skirt_mlp_destroy(skirt_mlp_t net)
     cudaFree(net->Wb);
     cudaFree(net->Bb);
     cudaFree(net->stats);
+    cudaFree(net->ws);
     delete net;
     return SKIRT_OK;
 }

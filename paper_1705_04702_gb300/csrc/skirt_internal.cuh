@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <vector>
 
 #include "skirt.h"
@@ -241,6 +242,10 @@ int mlp_forward_internal(skirt_mlp_s* net, const float* features, const double* 
 // after the stream has synchronised: INVALID (CUDA) when an inference launch
 // gave up waiting for a feature copy
 int mlp_check_timeout();
+// the network's working tables for skirt_dust_emission (at least `bytes`,
+// 256-byte aligned); the caller holds mlp_workspace_mutex(net) while it uses them
+std::mutex& mlp_workspace_mutex(skirt_mlp_s* net);
+int mlp_workspace(skirt_mlp_s* net, size_t bytes, void** p);
 // emission.cu: exact FP64 emission of rows (all rows when rows == NULL); a
 // second absorbed table [ncell][n2] with its shares (NULL: none) adds its power
 int launch_exact_emission(const double* absorbed, int n_in, const double* w_dev, const float* mass,
