@@ -48,6 +48,23 @@ def test_band_features_match_oracle(S, fields):
     np.testing.assert_allclose(feat.cpu().numpy(), x, rtol=3e-7, atol=1e-6)
 
 
+def test_band_features_into_an_unaligned_table(S, fields):
+    """Features written through a pointer that is 4 bytes past a 16-byte
+    boundary (a view one float into a buffer) equal the aligned result."""
+    import torch
+    lam, a, m = fields
+    n = a.shape[0]
+    ad, md = _dev(a, torch.float64), _dev(m, torch.float32)
+    feat = torch.zeros((n, 32), dtype=torch.float32, device="cuda")
+    tot = torch.zeros(n, dtype=torch.float64, device="cuda")
+    S.skirt_band_features(ad, n, lam.size, lam, md, feat, tot)
+    buf = torch.zeros(n * 32 + 1, dtype=torch.float32, device="cuda")
+    tot2 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    S.skirt_band_features(ad, n, lam.size, lam, md, buf[1:], tot2)
+    assert buf[1:].data_ptr() % 16 == 4
+    assert torch.equal(buf[1:].view(n, 32), feat) and torch.equal(tot2, tot) and buf[0].item() == 0.0
+
+
 def test_exact_emission_matches_oracle(S, fields):
     import torch
     lam, a, m = fields
