@@ -281,7 +281,10 @@ int skirt_autotune(skirt_grid_t grid, const skirt_source* src, const skirt_wavel
  *   B(lambda, T) = lambda^-5 / (exp(hc/(k lambda T)) - 1);
  *   energy balance M c_i G_i(T_i) = P_i, G_i(T) = sum_l W_l kappa_i B(lambda_l, T),
  *     c_i = 1/G_i(30 K), M = dust mass of the cell (extinction coefficient x volume);
- *     T_i by bracketed Newton on ln T in [3, 2000] K (FP64, clamped);
+ *     T_i by bracketed Newton on ln T in [3, 2000] K (clamped), accepted when the
+ *     step is below 1e-13 of ln T; the per-population steps run in FP64, the
+ *     Planck terms in double-float (~2e-14 relative; terms with
+ *     hc/(k lambda T) > 70, below 4e-23 of G_i, are left out);
  *   emission(m, l) = sum_i P_i W_l kappa_i B(lambda_l, T_i) / G_i(T_i)
  *     (luminosity in output bin l; the row sums to the absorbed power). */
 enum { SKIRT_EMIT_EXACT = 0, SKIRT_EMIT_SURROGATE = 1 };
@@ -382,7 +385,7 @@ typedef struct {
     float ms_features, ms_surrogate, ms_exact; /* device time of the three stages */
 } skirt_emission_stats;
 
-/* Emission of every cell from its absorbed spectrum.  mode EXACT: the FP64
+/* Emission of every cell from its absorbed spectrum.  mode EXACT: the exact
  * solver on every cell.  mode SURROGATE: band features -> MLP on every cell,
  * then the exact solver overwrites the rows whose features fall outside the
  * network's hull or guard (net required).  absorbed: device double[ncell][n_in];

@@ -3,10 +3,11 @@
 //
 //  * dust_mass_kernel      M = kappa*rho * cell volume
 //  * band_features_kernel  32 log-spaced band sums per unit mass (log10) and
-//                          the total absorbed power, one thread per cell
-//  * exact_kernel          FP64 equilibrium temperatures of three grain
-//                          populations by bracketed Newton on ln T, then the
-//                          energy-conserving emission spectrum
+//                          the total absorbed power, one cell per lane
+//  * exact_kernel          equilibrium temperatures of three grain
+//                          populations by bracketed Newton on ln T (FP64
+//                          per population, Planck terms in double-float),
+//                          then the energy-conserving emission spectrum
 // and skirt_dust_emission, which runs either the exact solver on every cell
 // or the MLP surrogate (mlp.cu) with the exact solver as the fallback for
 // cells outside the network's training hull.

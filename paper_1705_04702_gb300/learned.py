@@ -1,5 +1,5 @@
 """The learned form of the panchromatic run: stellar emission phase, dust
-emission from the absorbed field through the MLP surrogate (exact FP64
+emission from the absorbed field through the MLP surrogate (exact
 solver as fallback and as the reference the surrogate is scored against), and
 the dust re-emission trace (arXiv:1705.04702 Sect. 3.2, stellar emission phase -> dust emission phase).
 
