@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -481,6 +482,14 @@ extern "C" int skirt_trace(skirt_grid_t g, const skirt_source* src, const skirt_
     A.oct_nodes = g->oct_nodes;
     A.oct_leaf = g->oct_leaf;
     A.oct_step_cap = g->nx + g->ny + g->nz + 8;
+    // the mixed form's optical-depth cut-off; SKIRT_MIXED_TAU_CUT (a value above
+    // 30, e.g. 1e30 for none) moves it: a diagnostic showing that the cut
+    // changes no packet history
+    A.tau_cut = 30.f;
+    if (const char* e = std::getenv("SKIRT_MIXED_TAU_CUT")) {
+        const float v = std::strtof(e, nullptr);
+        if (v > 30.f) A.tau_cut = v;
+    }
     const int nn[3] = {g->nx, g->ny, g->nz};
     for (int a = 0; a < 3; ++a) {
         A.lo[a] = g->bbox[2 * a];

@@ -116,6 +116,8 @@ struct TraceArgs {
     const OctNode* oct_nodes;
     const int4* oct_leaf;                  // per leaf: lattice corner x, y, z and level
     int oct_step_cap;                      // crossings after which a traversal is abandoned
+    float tau_cut;                         // mixed form: optical depth at which a deposit or peel-off
+                                           // traversal stops (30; larger values are a diagnostic)
 };
 
 // trace.cu (FP64 form; dispatches the mixed form to trace_mixed.cu)

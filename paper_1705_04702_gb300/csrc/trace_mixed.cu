@@ -44,7 +44,6 @@ namespace {
 
 constexpr int MAXB = 256;       // threads per block of the mixed kernel (upper bound)
 constexpr int ROUND = 8;        // cell crossings per stepping round between warp votes
-constexpr float TAU_CUT = 30.f; // optical depth after which a deposit / peel-off traversal stops
 
 // FP32 -> FP64 by IEEE-754 field manipulation on the integer pipe: exact for
 // normal floats; zero and FP32 subnormals map to zero.
@@ -164,6 +163,7 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
     const float2* __restrict__ fz = A.faces + (nx + 1) + (ny + 1);
     double* __restrict__ absorbed = A.absorbed;
     const int step_min = A.step_min > 0 ? A.step_min : 20;
+    const float tau_cut = A.tau_cut;  // optical depth after which a deposit / peel-off traversal stops
 
     // ---- stepping state (registers)
     int mode = M_NONE;
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                 last_axis = axis;
             }
         }
-        if (tau_h > TAU_CUT && mode != M_LOCATE) done = true;
+        if (tau_h > tau_cut && mode != M_LOCATE) done = true;
         if (done) mode = M_NONE;
     };
 
@@ -399,12 +399,12 @@ __global__ void __launch_bounds__(MAXB, 3) trace_mixed_kernel(const TraceArgs A)
                 last_axis = axis;
             }
         }
-        // Beyond tau = TAU_CUT a line of sight transmits < e^-30 (1e-13) and a
+        // Beyond tau = tau_cut (30) a line of sight transmits < e^-30 (1e-13) and a
         // deposit path has handed < e^-30 of the luminosity to its remaining
         // cells; 1 - e^-tau is 1 in FP32 from tau = 17 on, so the forced
         // scattering draw does not change: the traversal ends there (the search
         // never gets that far, since tau_int < 17 in FP32).
-        if (tau_h > TAU_CUT && mode != M_LOCATE) done = true;
+        if (tau_h > tau_cut && mode != M_LOCATE) done = true;
         if (done) mode = M_NONE;
     };
 

@@ -338,3 +338,28 @@ def test_parity_criterion_detects_a_planted_mistake(S, oracle_lib, chaotic):
     with pytest.raises(AssertionError):
         check_mixed(S, oracle_lib, grid, prob, g, r, chaotic=chaotic)
     grid.close()
+
+
+def test_optical_depth_cut_changes_no_history(S, monkeypatch):
+    """The mixed form stops a deposit or peel-off traversal once its optical
+    depth passes 30.  Walking every path to the boundary instead
+    (SKIRT_MIXED_TAU_CUT=1e30) changes no packet history: scattering counts
+    and interaction points are bit-identical on the clumpy torus, and a
+    packet's luminosity fields move by less than 1e-12 (what the cut leaves
+    out is below e^-30 of a packet).  A table entry collects such tails over
+    many traversals, so the tables and ledgers are held to 1e-10."""
+    prob = W.torus_problem(n=48, nlambda=200, packet_scale=2e-4, npx=64)
+    grid = S.Grid(prob.grid)
+    a = S.run_problem(prob, grid, precision=S.PREC_MIXED, nrec=60)
+    monkeypatch.setenv("SKIRT_MIXED_TAU_CUT", "1e30")
+    b = S.run_problem(prob, grid, precision=S.PREC_MIXED, nrec=60)
+    grid.close()
+    ra, rb = _np(a["records"]), _np(b["records"])
+    assert np.array_equal(ra[..., 0], rb[..., 0])      # scatterings
+    assert np.array_equal(ra[..., 5:8], rb[..., 5:8])  # last interaction point
+    scale = np.abs(rb[..., 1:5]).max()
+    assert np.abs(ra[..., 1:5] - rb[..., 1:5]).max() <= 1e-12 * scale
+    compare_tally(_np(a["absorbed"]), _np(b["absorbed"]), 1e-10)
+    compare_tally(_np(a["images_flat"]), _np(b["images_flat"]), 1e-10)
+    for k in ("emitted", "absorbed", "escaped", "residual", "scatterings"):
+        assert a["ledger"][k] == pytest.approx(b["ledger"][k], rel=1e-10, abs=1e-10 * b["ledger"]["emitted"])
