@@ -61,6 +61,16 @@ const char* skirt_last_error(void);
 /* Library version string. */
 const char* skirt_version(void);
 
+/* Diagnostic environment variables (read at every call; results stay
+ * within the parity bars either way, so they serve tests that show what a
+ * reading of the method changes):
+ *   SKIRT_MIXED_TAU_CUT       mixed form: optical depth at which a deposit or
+ *                             peel-off traversal stops, if above the default 30
+ *                             (e.g. 1e30: walk every path to the boundary);
+ *   SKIRT_EXACT_TABLE_STRIDE  exact dust emission: start the Newton solves from
+ *                             every 2^k-th point (k <= 6) of the temperature
+ *                             table, so that they take more Newton steps. */
+
 /* ------------------------------------------------------------ dust grid */
 /* Setup (Sect. 3.2): the dust grid is the discretisation of the dust
  * distribution into cells.  Cartesian grid of nx*ny*nz cells over the box
