@@ -288,6 +288,39 @@ __device__ __forceinline__ double widen(float f)
 
 __device__ __forceinline__ double df_to_double(dfl::df2 v) { return widen(v.hi) + widen(v.lo); }
 
+// v * 2^e for a normal v: the exponent field moved on the integer pipe; a
+// result that would leave the normal range takes the multiplication
+__device__ __forceinline__ double scale_pow2(double v, int e)
+{
+    const long long u = __double_as_longlong(v);
+    const int ev = (int)((u >> 52) & 0x7FF);
+    if (ev == 0 || ev + e <= 0 || ev + e >= 0x7FF) return v * __longlong_as_double((long long)(e + 1023) << 52);
+    return __longlong_as_double(u + ((long long)e << 52));
+}
+
+// the warp sums of three values on every lane: one butterfly that halves the
+// set of partial sums a lane carries at the first two levels (6 FP64 adds
+// instead of 15); lanes 8k .. 8k+7 end with the sum of value k, broadcast
+__device__ __forceinline__ void warp_sum3(double& a, double& b, double& c)
+{
+    const int lane = threadIdx.x & 31;
+    const bool up = lane & 16;
+    // level 16: the lower half keeps (a, b), the upper half (c, 0)
+    double k0 = up ? c : a, k1 = up ? 0.0 : b;
+    const double s0 = up ? a : c, s1 = up ? b : 0.0;
+    k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+    k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+    // level 8: lanes with bit 3 keep the second value
+    const bool hi8 = lane & 8;
+    double k = hi8 ? k1 : k0;
+    k += __shfl_xor_sync(0xffffffffu, hi8 ? k0 : k1, 8);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+    a = __shfl_sync(0xffffffffu, k, 0);
+    b = __shfl_sync(0xffffffffu, k, 8);
+    c = __shfl_sync(0xffffffffu, k, 16);
+}
+
 __device__ __forceinline__ dfl::df2 df_from_double(double v)
 {
     const float h = __double2float_rn(v);
@@ -350,7 +383,7 @@ __device__ __forceinline__ float warp_sum_f(float v)
 // non-inlined routine: unrolled, the solve's code outgrew the instruction
 // cache and the warps stalled on instruction fetch.
 __device__ __forceinline__ void eval_row(const float4* __restrict__ slot, const dfl::df2 (&iT)[NPOP], unsigned on,
-                                         const dfl::df2 (&Pp)[NPOP], double scale, double* __restrict__ out,
+                                         const dfl::df2 (&Pp)[NPOP], int scale_e, double* __restrict__ out,
                                          float2* __restrict__ buf, int lane, dfl::df2 (&G)[NPOP], float (&D)[NPOP])
 {
     dfl::df2 g0 = dfl::make(0.f, 0.f), g1 = g0, g2 = g0;
@@ -382,7 +415,7 @@ __device__ __forceinline__ void eval_row(const float4* __restrict__ slot, const 
         const float2 b0 = buf[l], b1 = buf[NOUT + l], b2 = buf[2 * NOUT + l];
         const dfl::df2 e = dfl::add(dfl::add(dfl::mul(PS[0], dfl::make(b0.x, b0.y)), dfl::mul(PS[1], dfl::make(b1.x, b1.y))),
                                     dfl::mul(PS[2], dfl::make(b2.x, b2.y)));
-        __stcs(out + l, df_to_double(e) * scale);
+        __stcs(out + l, scale_pow2(df_to_double(e), scale_e));
     }
     __syncwarp();
 }
@@ -475,9 +508,7 @@ __global__ void __launch_bounds__(32 * EX_WARPS) exact_kernel(
                     p2 += __ldg(w2 + 2 * n2 + j) * v;
                 }
             }
-            p0 = warp_sum_bcast(p0);
-            p1 = warp_sum_bcast(p1);
-            p2 = warp_sum_bcast(p2);
+            warp_sum3(p0, p1, p2);
             if (my_r == r) {
                 P = my_i == 0 ? p0 : (my_i == 1 ? p1 : p2);
                 // binary exponent of the row's largest population power (0 if none is positive)
@@ -522,8 +553,7 @@ __global__ void __launch_bounds__(32 * EX_WARPS) exact_kernel(
             }
             const int Er = __shfl_sync(0xffffffffu, E, l0);
             const long long m = rows ? (long long)rows[base + r] : base + r;
-            eval_row(s_slot, iTr, (on_all >> l0) & 7u, Ppr, __longlong_as_double((long long)(Er + 1023) << 52),
-                     emission + (size_t)m * NOUT, buf, lane, G, D);
+            eval_row(s_slot, iTr, (on_all >> l0) & 7u, Ppr, Er, emission + (size_t)m * NOUT, buf, lane, G, D);
             if (my_r == r) {
                 Gm = my_i == 0 ? G[0] : (my_i == 1 ? G[1] : G[2]);
                 Dm = my_i == 0 ? D[0] : (my_i == 1 ? D[1] : D[2]);
@@ -582,8 +612,7 @@ __global__ void __launch_bounds__(32 * EX_WARPS) exact_kernel(
             }
             const int Er = __shfl_sync(0xffffffffu, E, l0);
             const long long m = rows ? (long long)rows[base + ri] : base + ri;
-            eval_row(s_slot, iTr, (on_all >> l0) & 7u, Ppr, __longlong_as_double((long long)(Er + 1023) << 52),
-                     emission + (size_t)m * NOUT, buf, lane, G, D);
+            eval_row(s_slot, iTr, (on_all >> l0) & 7u, Ppr, Er, emission + (size_t)m * NOUT, buf, lane, G, D);
         }
         if (temperature && mine) temperature[(size_t)my_m * NPOP + my_i] = (float)T;
     }
