@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=1)
     ap.add_argument("--batched-fp64-fraction", type=float, default=0.005,
                     help="plain FP64 sample of the batched form (fraction of its packets)")
-    ap.add_argument("--epochs", type=int, default=60, help="learned workload: training epochs")
+    ap.add_argument("--epochs", type=int, default=200, help="learned workload: training epochs")
+    ap.add_argument("--batch", type=int, default=2048, help="learned workload: training batch")
     ap.add_argument("--lr", type=float, default=2e-3, help="learned workload: Adam step size")
     ap.add_argument("--cells", type=int, default=2_000_000, help="exact workload: cells")
     ap.add_argument("--workload", default="disk",
@@ -304,7 +305,8 @@ def run_learned_report(args):
     from paper_1705_04702_gb300.learned import run_learned
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     rep = run_learned(n=args.grid, nlambda=200, packet_scale=args.packets / 1e8, n_train=1_000_000,
-                      n_test=100_000, epochs=args.epochs, lr=args.lr, reemit_per_lambda=1_000_000)
+                      n_test=100_000, epochs=args.epochs, batch=args.batch, lr=args.lr,
+                      reemit_per_lambda=1_000_000)
     rep = {k: v for k, v in rep.items() if not k.startswith("_")}
     print(json.dumps({"report": "learned form", "workload": f"clumpy torus {args.grid}^3, 200 wavelengths",
                       **rep}), flush=True)

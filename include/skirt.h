@@ -340,8 +340,8 @@ int skirt_mlp_get_params(skirt_mlp_t net, float* params, float* x_mean, float* x
                          float* hull_hi);
 
 typedef struct {
-    int epochs;          /* passes over the training set (default 60) */
-    int batch;           /* samples per Adam step (default 4096) */
+    int epochs;          /* passes over the training set (default 200) */
+    int batch;           /* samples per Adam step (default 2048) */
     float lr;            /* Adam step size (default 2e-3, cosine-decayed to lr/20) */
     float beta1, beta2, eps; /* Adam moments (defaults 0.9, 0.999, 1e-8) */
     uint64_t seed;       /* batch order */

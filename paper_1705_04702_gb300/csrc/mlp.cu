@@ -650,8 +650,8 @@ extern "C" int skirt_mlp_get_params(skirt_mlp_t net, float* params, float* x_mea
 extern "C" int skirt_mlp_train_opts_default(skirt_mlp_train_opts* o)
 {
     if (!o) return set_error(SKIRT_ERR_INVALID_ARG, "opts is NULL");
-    o->epochs = 60;
-    o->batch = 4096;
+    o->epochs = 200;
+    o->batch = 2048;
     o->lr = 2e-3f;
     o->beta1 = 0.9f;
     o->beta2 = 0.999f;

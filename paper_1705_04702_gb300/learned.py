@@ -21,7 +21,7 @@ def _sync():
     torch.cuda.synchronize()
 
 
-def run_learned(n=256, nlambda=200, packet_scale=1.0, n_train=1_000_000, n_test=100_000, epochs=60, batch=4096,
+def run_learned(n=256, nlambda=200, packet_scale=1.0, n_train=1_000_000, n_test=100_000, epochs=200, batch=2048,
                 lr=2e-3, reemit_per_lambda=1_000_000, seed=1, compare_exact=True, autotune=False, keep=False):
     """Runs the learned form on the clumpy torus and returns a report: stage
     times [s], the surrogate's error against the exact solver on held-out

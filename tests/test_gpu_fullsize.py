@@ -229,10 +229,12 @@ def test_learned_form_full_grid_sampled(S, oracle_lib):
     cells, 200 wavelengths; the absorbed table of the whole 7.5e8-packet
     stellar trace): band features and the exact emission on every cell, the
     oracle on 2000 sampled heated cells; energy exact on every cell; the
-    surrogate (trained on 1e6 cells, 60 epochs) energy-exact on every cell;
-    on every heated cell, after the guard's fallback, the median and the 99th
-    percentile of the per-cell error within 2% of the exact rows (the largest
-    error is reported)."""
+    surrogate (trained on 1e6 cells with the default 200 epochs of batch
+    2048) energy-exact on every cell; after the guard's fallback the median
+    error below 0.5%, the 99th percentile below 1%, at most 10 of the 6.7M
+    heated cells above 2% and none above 3% (measured: 0 to 2 cells above
+    2%, the largest 1.7-2.4% depending on the training sample: a few
+    isolated cells, which neither more epochs nor a tighter guard remove)."""
     import torch
     from oracle import emission as E
     prob = W.torus_problem(n=256, nlambda=200, npx=64)
@@ -272,7 +274,7 @@ def test_learned_form_full_grid_sampled(S, oracle_lib):
     # the surrogate on every cell
     tr = live[torch.randperm(live.numel(), device="cuda", generator=gen)[:1_000_000]]
     net = S.MLP(seed=6)
-    net.train(feat.index_select(0, tr).contiguous(), exact.index_select(0, tr).contiguous(), tr.numel(), epochs=60)
+    net.train(feat.index_select(0, tr).contiguous(), exact.index_select(0, tr).contiguous(), tr.numel())
     sur = torch.empty_like(exact)
     st = S.skirt_dust_emission(absorbed, ncell, nl, lam, mass, S.EMIT_SURROGATE, net, sur)
     net.close()
@@ -285,4 +287,5 @@ def test_learned_form_full_grid_sampled(S, oracle_lib):
     print("surrogate error over the heated cells: median", np.median(e), "p99", np.percentile(e, 99), "max", e.max(),
           "fallback", st["n_fallback"], "within 2%", (e <= 0.02).mean())
     assert st["n_fallback"] > 0
-    assert np.median(e) < 0.02 and np.percentile(e, 99) < 0.02, (np.median(e), np.percentile(e, 99))
+    assert np.median(e) < 0.005 and np.percentile(e, 99) < 0.01, (np.median(e), np.percentile(e, 99))
+    assert (e > 0.02).sum() <= 10 and e.max() < 0.03, ((e > 0.02).sum(), e.max())
