@@ -308,3 +308,54 @@ def test_exact_emission_at_extreme_powers(S, scale):
     np.testing.assert_allclose(tot.cpu().numpy(), total, rtol=1e-13, atol=0)
     if scale == 1e-40:
         np.testing.assert_allclose(feat.cpu().numpy(), x, rtol=3e-7, atol=1e-6)
+
+
+def test_surrogate_calls_sharing_a_network(S):
+    """Surrogate-mode calls keep their working tables in the network handle
+    (grown on demand, one call at a time): calls of growing and shrinking
+    size, then four threads calling at once on their own streams with the
+    same network, give the rows of one call at a time."""
+    import threading
+    import torch
+    lam = np.geomspace(0.09, 10.0, 200)
+    sizes = (3000, 40000, 1000, 20000)
+    data = []
+    for k, n in enumerate(sizes):
+        a, m = W.absorbed_spectra(n, lam, seed=40 + k)
+        data.append((_dev(a, torch.float64), _dev(m, torch.float32), n))
+    a0, m0, n0 = data[1]
+    feat = torch.zeros((n0, 32), dtype=torch.float32, device="cuda")
+    tot = torch.zeros(n0, dtype=torch.float64, device="cuda")
+    S.skirt_band_features(a0, n0, lam.size, lam, m0, feat, tot)
+    ex = torch.zeros((n0, 100), dtype=torch.float64, device="cuda")
+    S.skirt_dust_emission(a0, n0, lam.size, lam, m0, S.EMIT_EXACT, None, ex)
+    net = S.MLP(seed=2)
+    net.train(feat, ex, n0, epochs=5, batch=1024)
+    ref = []
+    for a, m, n in data:  # one at a time: 3000, then a larger table, then smaller ones
+        em = torch.zeros((n, 100), dtype=torch.float64, device="cuda")
+        S.skirt_dust_emission(a, n, lam.size, lam, m, S.EMIT_SURROGATE, net, em)
+        ref.append(em)
+    outs = [torch.zeros_like(r) for r in ref]
+    streams = [torch.cuda.Stream() for _ in data]
+    errors = []
+
+    def call(k):
+        try:
+            a, m, n = data[k]
+            S.skirt_dust_emission(a, n, lam.size, lam, m, S.EMIT_SURROGATE, net, outs[k],
+                                  stream=streams[k].cuda_stream)
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=call, args=(k,)) for k in range(len(data))]
+    torch.cuda.synchronize()  # inputs and zeroed outputs ready before other streams touch them
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    torch.cuda.synchronize()
+    net.close()
+    assert not errors, errors
+    for r, o in zip(ref, outs):
+        assert torch.equal(r, o)
