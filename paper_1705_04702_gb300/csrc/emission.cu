@@ -267,14 +267,6 @@ constexpr int EX_WARPS = 4;   // warps per block
 constexpr int EX_BATCH = 10;  // rows per warp batch: lanes 3r + i, r < 10
 constexpr float X_CUT = 70.f;
 
-
-__device__ __forceinline__ double warp_sum_bcast(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return __shfl_sync(0xffffffffu, v, 0);
-}
-
 // binary32 -> FP64 on the integer pipe: exact for normal numbers, zero for
 // zero and subnormals (which the double-float terms only reach below 1e-23
 // of a row)
