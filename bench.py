@@ -393,7 +393,7 @@ ISSUE_INST_PER_PACKET = 23468.0
 # DRAM bytes (read + write) per packet of the trace kernel from one ncu
 # capture of a 3e6-packet launch of the kernel as it stands (profiles/),
 # scaled by the packets of the launch; None when the kernel has changed since.
-TRAFFIC_PER_PACKET = {"disk": 30250.0, "octree": 102020.0}
+TRAFFIC_PER_PACKET = {"disk": 30254.0, "octree": 102039.0}
 
 
 def trace_rooflines(led, packets, k_ms, ninstr, red_rate, peak, peak_kind, kernel, crossing_bytes, traffic_pp,
