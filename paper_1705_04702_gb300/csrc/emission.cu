@@ -378,6 +378,15 @@ __device__ __forceinline__ void eval_row(const float4* __restrict__ slot, const 
                                          const dfl::df2 (&Pp)[NPOP], int scale_e, double* __restrict__ out,
                                          float2* __restrict__ buf, int lane, dfl::df2 (&G)[NPOP], float (&D)[NPOP])
 {
+    if (on == 0u) {  // no population absorbs (a dust-free or unheated cell): a zero row
+#pragma unroll
+        for (int i = 0; i < NPOP; ++i) {
+            G[i] = dfl::make(0.f, 0.f);
+            D[i] = 0.f;
+        }
+        for (int l = lane; l < NOUT; l += 32) __stcs(out + l, 0.0);
+        return;
+    }
     dfl::df2 g0 = dfl::make(0.f, 0.f), g1 = g0, g2 = g0;
     float d0 = 0.f, d1 = 0.f, d2 = 0.f;
 #pragma unroll 1
