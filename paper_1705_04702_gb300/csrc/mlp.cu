@@ -274,6 +274,21 @@ __global__ void __launch_bounds__(32 * INF_WARPS, 2) mlp_infer_kernel(
             // a cell without absorbed power emits nothing: no fallback needed
             if (lane < 16 && r < n) flags[r] = (mine && total[r] > 0.0) ? 1 : 0;
         }
+        // a tile none of whose rows absorbs power (empty space): its emission rows
+        // are zeros (the epilogue scales every row by its FP32 total), so the
+        // layers are skipped
+        if (!__any_sync(0xffffffffu, (float)tot0 != 0.f || (float)tot1 != 0.f)) {
+#pragma unroll
+            for (int j = 0; j < NO_PAD / 8; ++j) {
+                const int c = 8 * j + 2 * t;
+                if (c < NO) {
+                    if (r0 < n) __stcs(reinterpret_cast<double2*>(emission + r0 * NO + c), make_double2(0.0, 0.0));
+                    if (r1 < n) __stcs(reinterpret_cast<double2*>(emission + r1 * NO + c), make_double2(0.0, 0.0));
+                }
+            }
+            __syncwarp();  // every lane is done with this buffer before it is refilled
+            continue;
+        }
         uint32_t a1[2][4];
 #pragma unroll
         for (int kk = 0; kk < 2; ++kk) {

@@ -168,6 +168,42 @@ def test_tensor_core_inference_matches_oracle(S):
     net.close()
 
 
+def test_inference_skips_tiles_without_absorbed_power(S):
+    """Rows without absorbed power emit nothing; a 16-row tile of such rows
+    skips the network and writes zero rows.  Whole empty tiles, a tile with
+    one live row, and scattered zero rows: the zero rows are exactly zero and
+    the others follow the oracle's BF16 forward pass as in the dense test."""
+    import torch
+    rng = np.random.default_rng(13)
+    P = _small_params(7)
+    Pb = S.unpack_params(S.pack_params(P))
+    Pb = {k: (E.bf16_round(v) if k.startswith("W") else v) for k, v in Pb.items()}
+    mean = rng.normal(size=32).astype(np.float32)
+    std = (0.5 + rng.random(32)).astype(np.float32)
+    net = S.MLP(seed=1)
+    net.set_params(S.pack_params(P), mean, std, np.full(32, -1e30, np.float32), np.full(32, 1e30, np.float32))
+    n = 200 + 7
+    x = (mean + std * rng.normal(size=(n, 32)) * 0.8).astype(np.float32)
+    tot = 10 ** rng.uniform(-3, 3, n)
+    tot[0:48] = 0.0            # three whole tiles of empty cells
+    tot[64:80] = 0.0
+    tot[71] = 2.5              # ... one live row in the tile 64..79
+    tot[100::7] = 0.0          # scattered zero rows in live tiles
+    tot[200:] = 0.0            # an empty ragged tail
+    em = torch.full((n, 100), -1.0, dtype=torch.float64, device="cuda")
+    net.forward(_dev(x, torch.float32), _dev(tot, torch.float64), n, em)
+    g = em.cpu().numpy()
+    zero = tot == 0.0
+    assert np.all(g[zero] == 0.0)
+    xs = (x.astype(np.float64) - mean) / std.astype(np.float64)
+    p, _ = E.mlp_forward(Pb, xs, act_bf16=True)
+    ref = p[~zero] * tot[~zero][:, None]
+    rel = np.abs(g[~zero] - ref) / ref
+    assert np.percentile(rel, 99) < 2e-3 and rel.max() < 3e-2
+    np.testing.assert_allclose(g[~zero].sum(axis=1), tot[~zero], rtol=1e-5)
+    net.close()
+
+
 def test_training_reaches_two_percent_and_fallback_is_exact(S):
     """Train on exact solutions of synthetic fields; held-out emission within
     2% (per-cell relative L2, median and 95th percentile); the surrogate mode
