@@ -65,6 +65,31 @@ def test_band_features_into_an_unaligned_table(S, fields):
     assert torch.equal(buf[1:].view(n, 32), feat) and torch.equal(tot2, tot) and buf[0].item() == 0.0
 
 
+def test_band_features_with_empty_cell_runs(S):
+    """Runs of 32 empty cells (a warp's rows) skip the FP64 adds of their
+    staged blocks; the band closures still run. Cases: whole empty tiles,
+    a tile whose only power starts in its second column block, one whose
+    power ends in its first block, one whose power sits in the ragged last
+    block (200 = 6 x 32 + 8 columns), and an empty ragged tail of 13 cells."""
+    import torch
+    lam = np.geomspace(0.09, 10.0, 200)
+    n = 32 * 8 + 13
+    a, m = W.absorbed_spectra(n, lam, seed=23)
+    a[0:160] = 0.0
+    a[256:] = 0.0
+    a2, _ = W.absorbed_spectra(3, lam, seed=29)
+    a[70, 40:] = a2[0, 40:]
+    a[100, :20] = a2[1, :20]
+    a[159, 192:] = a2[2, 192:]
+    feat = torch.zeros((n, 32), dtype=torch.float32, device="cuda")
+    tot = torch.zeros(n, dtype=torch.float64, device="cuda")
+    S.skirt_band_features(_dev(a, torch.float64), n, lam.size, lam, _dev(m, torch.float32), feat, tot)
+    B, x, total = E.band_features(a, lam, m.astype(np.float64))
+    np.testing.assert_allclose(tot.cpu().numpy(), total, rtol=1e-13, atol=0)
+    np.testing.assert_allclose(feat.cpu().numpy(), x, rtol=3e-7, atol=1e-6)
+    assert np.count_nonzero(total[:160]) == 3 and np.all(total[256:] == 0)
+
+
 def test_exact_emission_matches_oracle(S, fields):
     import torch
     lam, a, m = fields
