@@ -190,6 +190,14 @@ def test_tensor_core_inference_matches_oracle(S):
     expect = np.any((x < lo) | (x > hi), axis=1) | (share > np.float32(thr))
     tie = np.abs(share / np.float32(thr) - 1.0) < 1e-5
     assert np.array_equal(f[~tie], expect[~tie]) and expect.sum() > 150
+    # absorbed powers 8 bytes past a 16-byte boundary: the same rows and flags
+    tbuf = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+    tbuf[1:] = _dev(tot, torch.float64)
+    assert tbuf[1:].data_ptr() % 16 == 8
+    em2 = torch.zeros_like(em)
+    flags2 = torch.zeros_like(flags)
+    net.forward(_dev(x, torch.float32), tbuf[1:], n, em2, flags2)
+    assert torch.equal(em2, em) and torch.equal(flags2, flags)
     net.close()
 
 
