@@ -154,14 +154,15 @@ __device__ __forceinline__ float narrow_trunc(double x)
 // grid).  One cell per lane, 32 cells per warp pass.  The warp walks the
 // input wavelengths in order in blocks of 32 columns; each block of its 32
 // rows is copied to shared memory by asynchronous copies (one 256-byte row
-// segment per instruction, coalesced), which keep the kernel at 62 registers
+// segment per instruction, coalesced), which keep the kernel at 64 registers
 // and 16 warps per SM (a register-staged block took 148 registers, 12 warps
 // per SM, and 18% longer).  Each lane sums its row's bands in wavelength
 // order (FP64) and, as the walk passes each band's end, adds the band sum to
 // the cell's total (FP64, band order): per cell about n_in/32 + 1 FP64 warp
 // instructions, a floor near the HBM time on GB300; each lane's serial walk
-// and the staging latency set the rest.  32 empty cells in a row skip their
-// FP64 adds.  The features are formed in FP32 and
+// and the staging latency set the rest.  The walk adds each band's columns of
+// a block in one inner loop (the next band end held in a register); 32 empty
+// cells in a row skip their FP64 adds.  The features are formed in FP32 and
 // leave through a shared-memory transpose as coalesced rows.
 constexpr int BF_WARPS = 2;  // warps per block
 static_assert(NB == 32, "32 bands");
@@ -183,7 +184,8 @@ __global__ void __launch_bounds__(32 * BF_WARPS) band_features_kernel(
         const int nrow = ncell - base < 32 ? (int)(ncell - base) : 32;
         int b = 0;
         double sb = 0.0, tot = 0.0;
-        bool live = false;  // warp-uniform: some staged block of these rows held a nonzero value
+        int nxt = s_start[1];  // the first column after band b
+        bool live = false;     // warp-uniform: some staged block of these rows held a nonzero value
         for (int c0 = 0; c0 < n_in; c0 += 32) {
             const bool col_ok = c0 + lane < n_in;
             // the block's 32 row segments straight into shared memory (8-byte
@@ -216,23 +218,28 @@ __global__ void __launch_bounds__(32 * BF_WARPS) band_features_kernel(
                 live = __any_sync(0xffffffffu, bits != 0ull);
             }
             if (live) {
-                for (int jj = 0; jj < cend; ++jj) {
+                int jj = 0;
+                while (jj < cend) {
                     // close the bands that end before this column (empty ones included)
-                    while (b < NB && s_start[b + 1] <= c0 + jj) {
+                    while (b < NB && nxt <= c0 + jj) {
                         band[lane][b] = narrow_trunc(sb);
                         tot += sb;
                         sb = 0.0;
                         ++b;
+                        nxt = b < NB ? s_start[b + 1] : 0x7fffffff;
                     }
-                    sb += tile[lane][jj];
+                    // the columns of band b in this block, in order
+                    const int seg = nxt - c0 < cend ? nxt - c0 : cend;
+                    for (; jj < seg; ++jj) sb += tile[lane][jj];
                 }
             } else {
                 // the same closures, with no column to add
-                while (b < NB && s_start[b + 1] <= c0 + cend - 1) {
+                while (b < NB && nxt <= c0 + cend - 1) {
                     band[lane][b] = narrow_trunc(sb);
                     tot += sb;
                     sb = 0.0;
                     ++b;
+                    nxt = b < NB ? s_start[b + 1] : 0x7fffffff;
                 }
             }
         }
