@@ -1,7 +1,6 @@
 """Pins of the dust-emission oracle and of its surrogate network's reference
 arithmetic against closed forms and finite differences."""
 import math
-import warnings
 
 import numpy as np
 import pytest
