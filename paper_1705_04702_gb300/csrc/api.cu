@@ -757,7 +757,7 @@ extern "C" int skirt_autotune(skirt_grid_t g, const skirt_source* src, const ski
         for (int ci = 0; ci < 3; ++ci)
             for (int si = 0; si < (mixed ? 3 : 1); ++si)
                 for (int bps = maxbps; bps >= 1; bps = (bps > 1 ? (bps + 1) / 2 : 0)) {
-                    skirt_tune_point p{blocks[bi], chunks[ci], bps, mixed ? step_mins[si] : 20, 0.f};
+                    skirt_tune_point p{blocks[bi], chunks[ci], bps, mixed ? step_mins[si] : 20, 0.f, 0.f};
                     const skirt_tune_point& d = cand[0];
                     const bool same = p.block == d.block && p.chunk == d.chunk && p.blocks_per_sm == d.blocks_per_sm &&
                                       (!mixed || p.step_min == d.step_min);
