@@ -398,7 +398,7 @@ TRAFFIC_PER_PACKET = {"disk": 30254.0, "octree": 102039.0}
 
 def trace_rooflines(led, packets, k_ms, ninstr, red_rate, peak, peak_kind, kernel, crossing_bytes, traffic_pp,
                     clock_mhz=None, sm_count=None):
-    """Rooflines of one trace launch (SURVEY 8(d)-style): algorithmic bytes
+    """Rooflines of one trace launch: algorithmic bytes
     (the crossing's read, a 16-byte read-modify-write per deposit and per
     peel-off tally) against the measured copy bandwidth; FP64 reductions (one
     per deposit and per tally) against the random red.f64 rate measured in the
